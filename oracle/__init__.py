@@ -1,0 +1,154 @@
+"""CPU oracle for the all-pairs minimax-path matrix -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU baseline /
+reference arm may import this package.  The product (the CUDA library and its
+binding) never does; it shares no code with ``appd_oracle.c``.
+
+Functions take a dense symmetric ``numpy`` matrix of dtype float32 or uint32 and
+return the matrix of original weight bits in the same dtype (diagonal 0):
+
+- ``appd(W)``: Prim + descending Algorithm 4 (Sections 3 and 5).
+- ``appd_ascending(W)``: the ascending alternative of Section 3.
+- ``fw(W)``: (min,max) Floyd-Warshall (Section 1, Table 1), n <= 4096.
+- ``brute(W)``: all simple paths, Eq. 1-2, n <= 9.
+- ``prim(W)``: Prim order and the MST edge codes.
+- ``tree_rows(W, mst, sources)``: rows of M by traversing the MST.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+_LIB = None
+
+F32, U32 = 0, 1
+
+
+def build() -> str:
+    """Compile the oracle with gcc (plain C, -O2, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, "liboracle.so")
+    src = os.path.join(_HERE, "appd_oracle.c")
+    if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-shared", "-fPIC",
+                               "-o", tmp, src])
+        os.replace(tmp, out)
+    return out
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            lib = ctypes.CDLL(build())
+            vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            lib.appd_oracle_alg4.argtypes = [vp, i64, ci, vp, vp]
+            lib.appd_oracle_ascending.argtypes = [vp, i64, ci, vp]
+            lib.appd_oracle_fw.argtypes = [vp, i64, ci, vp]
+            lib.appd_oracle_brute.argtypes = [vp, i64, ci, vp]
+            lib.appd_oracle_prim.argtypes = [vp, i64, ci, vp, vp]
+            lib.appd_oracle_tree_rows.argtypes = [vp, i64, ci, vp, vp, i64, vp]
+            lib.appd_oracle_set_mutation.argtypes = [ci]
+            lib.appd_oracle_order_key.argtypes = [ctypes.c_uint32, ci]
+            lib.appd_oracle_order_key.restype = ctypes.c_uint32
+            _LIB = lib
+    return _LIB
+
+
+def _prep(W: np.ndarray):
+    if W.dtype == np.float32:
+        dt = F32
+    elif W.dtype == np.uint32:
+        dt = U32
+    else:
+        raise TypeError(f"oracle takes float32 or uint32, got {W.dtype}")
+    if W.ndim != 2 or W.shape[0] != W.shape[1]:
+        raise ValueError("W must be square")
+    Wc = np.ascontiguousarray(W)
+    return Wc, Wc.shape[0], dt
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError(f"{what} failed with code {rc}")
+
+
+def appd(W: np.ndarray, *, return_fill_count: bool = False):
+    Wc, n, dt = _prep(W)
+    M = np.empty_like(Wc)
+    cnt = ctypes.c_int64(0)
+    _check(_lib().appd_oracle_alg4(Wc.ctypes.data, n, dt, M.ctypes.data, ctypes.byref(cnt)),
+           "appd_oracle_alg4")
+    return (M, cnt.value) if return_fill_count else M
+
+
+def appd_ascending(W: np.ndarray) -> np.ndarray:
+    Wc, n, dt = _prep(W)
+    M = np.empty_like(Wc)
+    _check(_lib().appd_oracle_ascending(Wc.ctypes.data, n, dt, M.ctypes.data),
+           "appd_oracle_ascending")
+    return M
+
+
+def fw(W: np.ndarray) -> np.ndarray:
+    Wc, n, dt = _prep(W)
+    M = np.empty_like(Wc)
+    _check(_lib().appd_oracle_fw(Wc.ctypes.data, n, dt, M.ctypes.data), "appd_oracle_fw")
+    return M
+
+
+def brute(W: np.ndarray) -> np.ndarray:
+    Wc, n, dt = _prep(W)
+    M = np.empty_like(Wc)
+    _check(_lib().appd_oracle_brute(Wc.ctypes.data, n, dt, M.ctypes.data), "appd_oracle_brute")
+    return M
+
+
+def prim(W: np.ndarray):
+    """Return (order, mst_codes): Prim order from vertex 0 and the n-1 edge codes.
+
+    mst_codes[k] = key << 32 | lo << 16 | hi of the edge that added order[k+1].
+    """
+    Wc, n, dt = _prep(W)
+    order = np.empty(n, dtype=np.uint32)
+    mst = np.empty(max(n - 1, 1), dtype=np.uint64)
+    _check(_lib().appd_oracle_prim(Wc.ctypes.data, n, dt, mst.ctypes.data, order.ctypes.data),
+           "appd_oracle_prim")
+    return order, mst[: n - 1]
+
+
+def tree_rows(W: np.ndarray, mst: np.ndarray, sources) -> np.ndarray:
+    Wc, n, dt = _prep(W)
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.uint32))
+    mst = np.ascontiguousarray(mst, dtype=np.uint64)
+    rows = np.empty((len(src), n), dtype=Wc.dtype)
+    _check(_lib().appd_oracle_tree_rows(Wc.ctypes.data, n, dt, mst.ctypes.data, src.ctypes.data,
+                                        len(src), rows.ctypes.data), "appd_oracle_tree_rows")
+    return rows
+
+
+def order_key(bits: int, dtype: int) -> int:
+    return int(_lib().appd_oracle_order_key(bits, dtype))
+
+
+class mutation:
+    """Context manager that plants mistake ``k`` in the oracle (tests only)."""
+
+    def __init__(self, k: int):
+        self.k = k
+
+    def __enter__(self):
+        _lib().appd_oracle_set_mutation(self.k)
+        return self
+
+    def __exit__(self, *exc):
+        _lib().appd_oracle_set_mutation(0)
+        return False

@@ -1,0 +1,526 @@
+/*
+ * oracle/appd_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, single-threaded CPU oracle for the all-pairs minimax-path
+ * (APPD / MMJ) distance matrix of a dense undirected complete graph
+ * (arxiv 2407.07058).  Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference arm may build, load or call this file.  It shares
+ * no code, header, table or helper with the CUDA library.
+ *
+ * What it computes (Eq. 1-2, Section 1): M(i,j) = min over all i-j paths p of
+ * the largest edge weight on p.  The main routine follows the paper's recipe
+ * (Section 3 and the proof in Section 5): build a minimum spanning tree with
+ * Prim's algorithm in O(n^2), sort its n-1 edges in descending order, remove
+ * them one by one from large to small; every removal splits the sub-tree that
+ * holds the edge into tree1 and tree2, both sides are found by traversal, and
+ * every pair (p in tree1, q in tree2) gets M(p,q) = M(q,p) = w(e).
+ *
+ * Readings of points the paper leaves open (each also listed in the design doc):
+ *  - Weights are compared by an order key: uint32 weights compare as
+ *    unsigned integers; FP32 weights compare by IEEE-754 totalOrder
+ *    (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN).  The output cell holds
+ *    the selected input weight's original bit pattern.
+ *  - Ties (Section 5 says they do not matter): edges are compared by the
+ *    triple (key, min endpoint, max endpoint), a strict total order, so the
+ *    MST and every sort below are deterministic.
+ *  - The diagonal M(i,i) is all-zero bits (+0.0f / 0u); W(i,i) is never read.
+ *  - W must be symmetric (an undirected graph, Section 1); only the upper
+ *    triangle W(i,j), i<j, is read as the weight of edge {i,j}.
+ *
+ * Test-only routines in this file: the ascending (small-to-large) form of
+ * Section 3, the (min,max) Floyd-Warshall variant named in Section 1 and
+ * Table 1, brute-force enumeration of simple paths (Eq. 1-2 written out),
+ * and per-source tree traversal for sampled rows at large n.
+ *
+ * A test can plant a mistake in this oracle (appd_oracle_set_mutation) to
+ * check that the pins catch it; mutation 0 is the correct oracle.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_F32 0
+#define OR_U32 1
+
+static int g_mutation = 0;
+
+void appd_oracle_set_mutation(int m) { g_mutation = m; }
+int appd_oracle_get_mutation(void) { return g_mutation; }
+
+/* Order key of one weight: unsigned compare on the key == IEEE totalOrder. */
+static uint32_t order_key(uint32_t bits, int dtype)
+{
+    if (dtype == OR_U32)
+        return bits;
+    if (bits & 0x80000000u)
+        return ~bits;            /* negative: larger magnitude sorts lower */
+    return bits | 0x80000000u;   /* non-negative: above every negative */
+}
+
+static uint32_t w_bits(const uint32_t *W, int64_t n, int64_t i, int64_t j)
+{
+    /* upper triangle is the edge weight */
+    return (i < j) ? W[i * n + j] : W[j * n + i];
+}
+
+/* Edge identity under the strict total order: key, then lo, then hi. */
+static uint64_t edge_code(const uint32_t *W, int64_t n, int dtype, int64_t a, int64_t b)
+{
+    int64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    uint64_t k = order_key(w_bits(W, n, lo, hi), dtype);
+    return (k << 32) | ((uint64_t)lo << 16) | (uint64_t)hi;
+}
+
+/* lo/hi live in 16 bits each; the oracle supports n <= 65536. */
+static int64_t code_lo(uint64_t c) { return (int64_t)((c >> 16) & 0xFFFF); }
+static int64_t code_hi(uint64_t c) { return (int64_t)(c & 0xFFFF); }
+
+/* ------------------------------------------------------------------ Prim */
+/*
+ * Prim's algorithm on the dense graph, O(n^2) (Section 3), from vertex 0.
+ * Outputs: mst[k] (edge code of the edge that added vertex order[k+1]),
+ * order[0..n-1] (the order vertices join the tree), delta[k] = key of mst[k].
+ * Mutation 3 flips the comparison (a maximum spanning tree: a wrong result
+ * for the minimax problem).
+ */
+int appd_oracle_prim(const uint32_t *W, int64_t n, int dtype,
+                     uint64_t *mst, uint32_t *order)
+{
+    if (n <= 0 || n > 65536)
+        return -1;
+    uint64_t *dist = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    unsigned char *in = (unsigned char *)calloc((size_t)n, 1);
+    if (!dist || !in) {
+        free(dist);
+        free(in);
+        return -2;
+    }
+    in[0] = 1;
+    order[0] = 0;
+    for (int64_t v = 1; v < n; ++v)
+        dist[v] = edge_code(W, n, dtype, 0, v);
+    for (int64_t step = 1; step < n; ++step) {
+        int64_t best = -1;
+        for (int64_t v = 0; v < n; ++v) {
+            if (in[v])
+                continue;
+            if (best < 0)
+                best = v;
+            else if (g_mutation == 3 ? dist[v] > dist[best] : dist[v] < dist[best])
+                best = v;
+        }
+        in[best] = 1;
+        order[step] = (uint32_t)best;
+        mst[step - 1] = dist[best];
+        for (int64_t v = 0; v < n; ++v) {
+            if (in[v])
+                continue;
+            uint64_t c = edge_code(W, n, dtype, best, v);
+            if (g_mutation == 3 ? c > dist[v] : c < dist[v])
+                dist[v] = c;
+        }
+    }
+    free(dist);
+    free(in);
+    return 0;
+}
+
+/* ------------------------------------------------------- MST adjacency */
+typedef struct {
+    int64_t n;
+    int64_t *off;    /* n+1 */
+    int64_t *nbr;    /* 2(n-1): neighbour vertex */
+    int64_t *eid;    /* 2(n-1): edge index */
+} tree_adj;
+
+static int build_adj(tree_adj *t, int64_t n, const uint64_t *edges, int64_t m)
+{
+    t->n = n;
+    t->off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    t->nbr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * m + 1));
+    t->eid = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * m + 1));
+    int64_t *fill = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!t->off || !t->nbr || !t->eid || !fill) {
+        free(fill);
+        return -2;
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        t->off[code_lo(edges[e]) + 1]++;
+        t->off[code_hi(edges[e]) + 1]++;
+    }
+    for (int64_t v = 0; v < n; ++v)
+        t->off[v + 1] += t->off[v];
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t a = code_lo(edges[e]), b = code_hi(edges[e]);
+        int64_t pa = t->off[a] + fill[a]++;
+        t->nbr[pa] = b;
+        t->eid[pa] = e;
+        int64_t pb = t->off[b] + fill[b]++;
+        t->nbr[pb] = a;
+        t->eid[pb] = e;
+    }
+    free(fill);
+    return 0;
+}
+
+static void free_adj(tree_adj *t)
+{
+    free(t->off);
+    free(t->nbr);
+    free(t->eid);
+}
+
+/* Iterative DFS over the current forest (edges with removed[e]==0). */
+static int64_t traverse(const tree_adj *t, const unsigned char *removed,
+                        int64_t start, int64_t *out, int64_t *stack,
+                        unsigned char *seen, int64_t *touched, int64_t *ntouched)
+{
+    int64_t cnt = 0, sp = 0;
+    stack[sp++] = start;
+    seen[start] = 1;
+    touched[(*ntouched)++] = start;
+    while (sp > 0) {
+        int64_t v = stack[--sp];
+        out[cnt++] = v;
+        for (int64_t k = t->off[v]; k < t->off[v + 1]; ++k) {
+            if (removed[t->eid[k]])
+                continue;
+            int64_t w = t->nbr[k];
+            if (seen[w])
+                continue;
+            seen[w] = 1;
+            touched[(*ntouched)++] = w;
+            stack[sp++] = w;
+        }
+    }
+    return cnt;
+}
+
+static int cmp_desc(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x < y) ? 1 : (x > y) ? -1 : 0;
+}
+
+static int cmp_asc(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x < y) ? -1 : (x > y) ? 1 : 0;
+}
+
+typedef struct {
+    uint64_t code;
+    int64_t idx;
+} code_idx;
+
+static int cmp_ci_desc(const void *a, const void *b)
+{
+    return cmp_desc(&((const code_idx *)a)->code, &((const code_idx *)b)->code);
+}
+
+static int cmp_ci_asc(const void *a, const void *b)
+{
+    return cmp_asc(&((const code_idx *)a)->code, &((const code_idx *)b)->code);
+}
+
+/* original bits of an MST edge, read back from W */
+static uint32_t edge_bits(const uint32_t *W, int64_t n, uint64_t code)
+{
+    return w_bits(W, n, code_lo(code), code_hi(code));
+}
+
+/*
+ * Algorithm 4 (MMJ distance by calculation and copy), Sections 3 and 5:
+ * descending removal of the MST edges; each removal fills the cross block of
+ * the two sub-trees.  If fill_count is not NULL it receives how many cells
+ * were written (each off-diagonal cell must be written exactly once).
+ * Mutations: 1 sorts ascending instead of descending, 2 fills M(p,q) but not
+ * M(q,p), 4 skips the smallest edge (drops one term).
+ */
+int appd_oracle_alg4(const uint32_t *W, int64_t n, int dtype, uint32_t *M,
+                     int64_t *fill_count)
+{
+    if (n < 0 || n > 65536)
+        return -1;
+    if (n == 0)
+        return 0;
+    for (int64_t i = 0; i < n * n; ++i)
+        M[i] = 0;
+    if (fill_count)
+        *fill_count = 0;
+    if (n == 1)
+        return 0;
+    int64_t m = n - 1;
+    uint64_t *mst = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)m);
+    uint32_t *ord = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    if (!mst || !ord)
+        return -2;
+    int rc = appd_oracle_prim(W, n, dtype, mst, ord);
+    free(ord);
+    if (rc) {
+        free(mst);
+        return rc;
+    }
+    tree_adj t;
+    if (build_adj(&t, n, mst, m)) {
+        free(mst);
+        return -2;
+    }
+    /* removal order: large to small (Section 3); codes are distinct */
+    code_idx *sorted = (code_idx *)malloc(sizeof(code_idx) * (size_t)m);
+    unsigned char *removed = (unsigned char *)calloc((size_t)m, 1);
+    unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
+    int64_t *tree1 = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *tree2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!sorted || !removed || !seen || !tree1 || !tree2 || !stack || !touched)
+        return -2;
+    for (int64_t e = 0; e < m; ++e) {
+        sorted[e].code = mst[e];
+        sorted[e].idx = e;
+    }
+    qsort(sorted, (size_t)m, sizeof(code_idx), g_mutation == 1 ? cmp_ci_asc : cmp_ci_desc);
+    int64_t filled = 0;
+    int64_t last = (g_mutation == 4) ? m - 1 : m;
+    for (int64_t k = 0; k < last; ++k) {
+        int64_t e = sorted[k].idx;
+        removed[e] = 1;
+        uint32_t bits = edge_bits(W, n, mst[e]);
+        int64_t nt = 0;
+        int64_t c1 = traverse(&t, removed, code_lo(mst[e]), tree1, stack, seen, touched, &nt);
+        int64_t c2 = traverse(&t, removed, code_hi(mst[e]), tree2, stack, seen, touched, &nt);
+        for (int64_t a = 0; a < nt; ++a)
+            seen[touched[a]] = 0;
+        for (int64_t a = 0; a < c1; ++a) {
+            int64_t p = tree1[a];
+            for (int64_t b = 0; b < c2; ++b) {
+                int64_t q = tree2[b];
+                M[p * n + q] = bits;
+                if (g_mutation != 2)
+                    M[q * n + p] = bits;
+                filled += (g_mutation != 2) ? 2 : 1;
+            }
+        }
+    }
+    if (fill_count)
+        *fill_count = filled;
+    free(sorted);
+    free(removed);
+    free(seen);
+    free(tree1);
+    free(tree2);
+    free(stack);
+    free(touched);
+    free(mst);
+    free_adj(&t);
+    return 0;
+}
+
+/* ----------------------------------------------- ascending form (test) */
+/*
+ * The ascending alternative of Section 3: add the MST edges from small to
+ * large into an empty forest (union-find); each union fills the cross
+ * product of the two member lists.
+ */
+int appd_oracle_ascending(const uint32_t *W, int64_t n, int dtype, uint32_t *M)
+{
+    if (n < 0 || n > 65536)
+        return -1;
+    for (int64_t i = 0; i < n * n; ++i)
+        M[i] = 0;
+    if (n <= 1)
+        return 0;
+    int64_t m = n - 1;
+    uint64_t *mst = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)m);
+    uint32_t *ord = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *tail = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!mst || !ord || !parent || !head || !tail || !next)
+        return -2;
+    int rc = appd_oracle_prim(W, n, dtype, mst, ord);
+    if (rc)
+        return rc;
+    qsort(mst, (size_t)m, sizeof(uint64_t), cmp_asc);
+    for (int64_t v = 0; v < n; ++v) {
+        parent[v] = v;
+        head[v] = v;
+        tail[v] = v;
+        next[v] = -1;
+    }
+    for (int64_t k = 0; k < m; ++k) {
+        int64_t a = code_lo(mst[k]), b = code_hi(mst[k]);
+        while (parent[a] != a)
+            a = parent[a] = parent[parent[a]];
+        while (parent[b] != b)
+            b = parent[b] = parent[parent[b]];
+        uint32_t bits = edge_bits(W, n, mst[k]);
+        for (int64_t p = head[a]; p >= 0; p = next[p])
+            for (int64_t q = head[b]; q >= 0; q = next[q]) {
+                M[p * n + q] = bits;
+                M[q * n + p] = bits;
+            }
+        /* union: append b's list to a's */
+        parent[b] = a;
+        next[tail[a]] = head[b];
+        tail[a] = tail[b];
+    }
+    free(mst);
+    free(ord);
+    free(parent);
+    free(head);
+    free(tail);
+    free(next);
+    return 0;
+}
+
+/* ------------------------------------------- (min,max) Floyd-Warshall */
+/* The (min,max) variant of Floyd-Warshall (Section 1, Table 1), O(n^3). */
+int appd_oracle_fw(const uint32_t *W, int64_t n, int dtype, uint32_t *M)
+{
+    if (n < 0 || n > 4096)
+        return -1;
+    uint32_t *K = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n * n + 1));
+    uint32_t *B = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n * n + 1));
+    if (!K || !B)
+        return -2;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            if (i == j) {
+                K[i * n + j] = 0;   /* identity of max: never the path max */
+                B[i * n + j] = 0;
+            } else {
+                uint32_t b = w_bits(W, n, i, j);
+                K[i * n + j] = order_key(b, dtype);
+                B[i * n + j] = b;
+            }
+        }
+    for (int64_t k = 0; k < n; ++k)
+        for (int64_t i = 0; i < n; ++i) {
+            if (i == k)
+                continue;
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == k || j == i)
+                    continue;
+                uint32_t a = K[i * n + k], c = K[k * n + j];
+                uint32_t mk = a > c ? a : c;
+                uint32_t mb = a > c ? B[i * n + k] : B[k * n + j];
+                if (mk < K[i * n + j]) {
+                    K[i * n + j] = mk;
+                    B[i * n + j] = mb;
+                }
+            }
+        }
+    memcpy(M, B, sizeof(uint32_t) * (size_t)(n * n));
+    free(K);
+    free(B);
+    return 0;
+}
+
+/* ------------------------------------------------ brute force, n <= 9 */
+/*
+ * Eq. 1-2 written out: for every pair, enumerate every simple path, take the
+ * largest edge key on it, and keep the smallest such maximum.  Equal keys
+ * always carry equal bits (the key is a bijection of the bits).
+ */
+static void bf_walk(const uint32_t *W, int64_t n, int dtype, int64_t v, int64_t target,
+                    unsigned char *on, int have, uint32_t cur_key, uint32_t cur_bits,
+                    int *found, uint32_t *best_key, uint32_t *best_bits)
+{
+    if (v == target) {
+        if (have && (!*found || cur_key < *best_key)) {
+            *found = 1;
+            *best_key = cur_key;
+            *best_bits = cur_bits;
+        }
+        return;
+    }
+    for (int64_t w = 0; w < n; ++w) {
+        if (on[w])
+            continue;
+        uint32_t b = w_bits(W, n, v, w);
+        uint32_t k = order_key(b, dtype);
+        int take = !have || k > cur_key;
+        on[w] = 1;
+        bf_walk(W, n, dtype, w, target, on, 1, take ? k : cur_key, take ? b : cur_bits,
+                found, best_key, best_bits);
+        on[w] = 0;
+    }
+}
+
+int appd_oracle_brute(const uint32_t *W, int64_t n, int dtype, uint32_t *M)
+{
+    if (n < 0 || n > 9)
+        return -1;
+    unsigned char on[16];
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            M[i * n + j] = 0;
+            if (i == j)
+                continue;
+            memset(on, 0, sizeof(on));
+            on[i] = 1;
+            int found = 0;
+            uint32_t bk = 0, bb = 0;
+            bf_walk(W, n, dtype, i, j, on, 0, 0, 0, &found, &bk, &bb);
+            M[i * n + j] = bb;
+        }
+    return 0;
+}
+
+/* -------------------------------------- sampled rows at large n (test) */
+/*
+ * Given the MST (edge codes) of a graph, fill rows of M for the listed
+ * sources by one traversal of the tree per source: M(s,v) is the largest
+ * edge on the unique tree path (Section 2.1: tree paths of an MST are minimax
+ * paths).  rows is (nsrc x n), row k for source src[k].
+ */
+int appd_oracle_tree_rows(const uint32_t *W, int64_t n, int dtype, const uint64_t *mst,
+                          const uint32_t *src, int64_t nsrc, uint32_t *rows)
+{
+    (void)dtype;
+    if (n <= 0 || n > 65536)
+        return -1;
+    int64_t m = n - 1;
+    tree_adj t;
+    if (build_adj(&t, n, mst, m))
+        return -2;
+    int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    uint64_t *best = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n); /* max code on path */
+    unsigned char *seen = (unsigned char *)malloc((size_t)n);
+    if (!stack || !best || !seen)
+        return -2;
+    for (int64_t k = 0; k < nsrc; ++k) {
+        int64_t s = src[k];
+        memset(seen, 0, (size_t)n);
+        int64_t sp = 0;
+        stack[sp++] = s;
+        seen[s] = 1;
+        best[s] = 0;
+        uint32_t *row = rows + k * n;
+        row[s] = 0;
+        while (sp > 0) {
+            int64_t v = stack[--sp];
+            for (int64_t a = t.off[v]; a < t.off[v + 1]; ++a) {
+                int64_t w = t.nbr[a];
+                if (seen[w])
+                    continue;
+                seen[w] = 1;
+                uint64_t c = mst[t.eid[a]];
+                best[w] = (v == s || c > best[v]) ? c : best[v];
+                row[w] = edge_bits(W, n, best[w]);
+                stack[sp++] = w;
+            }
+        }
+    }
+    free(stack);
+    free(best);
+    free(seen);
+    free_adj(&t);
+    return 0;
+}
+
+/* order key, exported so tests can check the key against its definition */
+uint32_t appd_oracle_order_key(uint32_t bits, int dtype) { return order_key(bits, dtype); }

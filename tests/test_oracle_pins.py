@@ -1,0 +1,344 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle (Prim + Algorithm 4, Sections 3 and 5) is checked against things
+that do not share its code or its algorithm:
+
+- hand-worked examples in tests/golden/ (Eq. 1-2 applied by hand);
+- a Python enumeration of every simple path (Eq. 1-2 written out again);
+- threshold connectivity: M(i,j) is the smallest weight t such that i and j
+  are connected by edges of weight <= t (an equivalent characterisation of
+  the minimax distance, computed with scipy's connected components);
+- closed forms: points on a line, all-equal weights, n = 1 and n = 2, two
+  well-separated clusters;
+- invariants from the proof in Section 5 and from ultrametricity;
+- the planted-mistake test: each mutation of the oracle is caught.
+"""
+import itertools
+import struct
+
+import numpy as np
+import pytest
+from scipy.sparse.csgraph import connected_components
+
+import oracle
+import synth
+from tests import golden_io
+
+
+# ------------------------------------------------------------------ helpers
+def f32_bits(x: float) -> int:
+    return struct.unpack("<I", struct.pack("<f", x))[0]
+
+
+def keys_np(A: np.ndarray) -> np.ndarray:
+    """Order keys of a float32/uint32 array (pinned by test_order_key_total_order)."""
+    b = A.view(np.uint32).astype(np.uint64)
+    if A.dtype == np.uint32:
+        return b
+    neg = (b >> 31) == 1
+    return np.where(neg, (~b) & 0xFFFFFFFF, b | 0x80000000)
+
+
+def py_brute(W: np.ndarray) -> np.ndarray:
+    """Every simple path, Eq. 1-2, in plain Python (n <= 7)."""
+    n = W.shape[0]
+    K = keys_np(W)
+    out = np.zeros_like(W)
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            best = None
+            others = [v for v in range(n) if v not in (i, j)]
+            for r in range(len(others) + 1):
+                for mid in itertools.permutations(others, r):
+                    path = (i,) + mid + (j,)
+                    mk = max(K[path[t], path[t + 1]] for t in range(len(path) - 1))
+                    if best is None or mk < best:
+                        best = mk
+                        arg = max(range(len(path) - 1), key=lambda t: K[path[t], path[t + 1]])
+                        bi, bj = path[arg], path[arg + 1]
+            out[i, j] = W[bi, bj]
+    return out
+
+
+def threshold_connectivity(W: np.ndarray) -> np.ndarray:
+    """M(i,j) = smallest key t with i~j in the graph of edges with key <= t."""
+    n = W.shape[0]
+    K = keys_np(W)
+    off = ~np.eye(n, dtype=bool)
+    levels = np.unique(K[off])
+    res = np.full((n, n), -1, dtype=np.int64)
+    for t in levels:
+        adj = (K <= t) & off
+        _, lab = connected_components(adj.astype(np.int8), directed=False)
+        same = lab[:, None] == lab[None, :]
+        newly = same & (res < 0) & off
+        res[newly] = t
+    # map keys back to bits: take any edge with that key
+    out = np.zeros_like(W)
+    flatk, flatw = K[off], W.view(np.uint32)[off]
+    lut = dict(zip(flatk.tolist(), flatw.tolist()))
+    ob = out.view(np.uint32)
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                ob[i, j] = lut[int(res[i, j])]
+    return out
+
+
+def sym_random(n, rng, dtype, kind="uniform"):
+    if dtype == np.uint32:
+        hi = 3 if kind == "ties" else 1 << 16
+        A = rng.integers(0, hi, size=(n, n)).astype(np.uint32)
+    else:
+        if kind == "ties":
+            A = rng.integers(0, 3, size=(n, n)).astype(np.float32)
+        else:
+            A = rng.random((n, n)).astype(np.float32)
+    A = np.triu(A, 1)
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    return np.ascontiguousarray(A.astype(dtype))
+
+
+def bits_equal(A, B):
+    return np.array_equal(A.view(np.uint32), B.view(np.uint32))
+
+
+# -------------------------------------------------------------------- tests
+def test_order_key_total_order():
+    # IEEE-754 totalOrder, listed by hand: -NaN < -inf < -max < -1 < -min_sub
+    # < -0 < +0 < +min_sub < 1 < max < +inf < +NaN
+    vals = [0xFFC00000, 0xFF800000, 0xFF7FFFFF, 0xBF800000, 0x80000001, 0x80000000,
+            0x00000000, 0x00000001, 0x3F800000, 0x7F7FFFFF, 0x7F800000, 0x7FC00000]
+    ks = [oracle.order_key(v, oracle.F32) for v in vals]
+    assert ks == sorted(ks) and len(set(ks)) == len(ks)
+    kn = keys_np(np.array(vals, dtype=np.uint32).view(np.float32)).tolist()
+    assert kn == ks
+    for v in [0, 1, 77, 0xFFFF, 0xFFFFFFFF]:
+        assert oracle.order_key(v, oracle.U32) == v
+
+
+@pytest.mark.parametrize("path", golden_io.all_fixtures(), ids=lambda p: p.split("/")[-1])
+def test_golden_fixtures(path):
+    W, M = golden_io.load(path)
+    for fn in (oracle.appd, oracle.appd_ascending, oracle.fw, oracle.brute):
+        got = fn(W)
+        assert bits_equal(got, M), (fn.__name__, got, M)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.uint32])
+@pytest.mark.parametrize("kind", ["uniform", "ties"])
+def test_small_vs_python_enumeration(dtype, kind):
+    rng = np.random.default_rng(11)
+    for n in range(1, 7):
+        for _ in range(6):
+            W = sym_random(n, rng, dtype, kind)
+            ref = py_brute(W)
+            assert bits_equal(oracle.appd(W), ref)
+            assert bits_equal(oracle.brute(W), ref)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.uint32])
+@pytest.mark.parametrize("kind", ["uniform", "ties"])
+def test_vs_threshold_connectivity(dtype, kind):
+    rng = np.random.default_rng(12)
+    for n in (7, 8, 9, 23, 47):
+        W = sym_random(n, rng, dtype, kind)
+        ref = threshold_connectivity(W)
+        assert bits_equal(oracle.appd(W), ref)
+        if n <= 9:
+            assert bits_equal(oracle.brute(W), ref)
+
+
+def test_fw_and_ascending_agree():
+    rng = np.random.default_rng(13)
+    cases = [sym_random(n, rng, dt, k) for n in (2, 3, 17, 64, 200)
+             for dt in (np.float32, np.uint32) for k in ("uniform", "ties")]
+    cases.append(synth.euclid(synth.gmm_points(256, 2, 5, sigma=0.5, seed=9, mean_box=10.0)))
+    cases.append(synth.hash_u32(300, seed=7))
+    for W in cases:
+        A = oracle.appd(W)
+        assert bits_equal(A, oracle.fw(W))
+        assert bits_equal(A, oracle.appd_ascending(W))
+
+
+def test_closed_form_points_on_a_line():
+    # 1-D Euclidean distances: M(i,j) is the largest gap between consecutive
+    # sorted coordinates between x_i and x_j (every path must cross each gap).
+    rng = np.random.default_rng(14)
+    x = (rng.random(150) * 100).astype(np.float32)
+    W = synth.euclid(x[:, None])
+    srt = np.argsort(x, kind="stable")
+    xs = x[srt].astype(np.float64)
+    gaps = np.abs(xs[1:] - xs[:-1]).astype(np.float32)  # |a-b| rounded once to f32
+    rank = np.empty(len(x), dtype=np.int64)
+    rank[srt] = np.arange(len(x))
+    n = len(x)
+    ref = np.zeros((n, n), dtype=np.float32)
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                a, b = sorted((rank[i], rank[j]))
+                ref[i, j] = gaps[a:b].max()
+    assert bits_equal(oracle.appd(W), ref)
+
+
+def test_closed_forms_degenerate():
+    assert bits_equal(oracle.appd(np.zeros((1, 1), np.float32)), np.zeros((1, 1), np.float32))
+    W2 = np.array([[0, 2.5], [2.5, 0]], dtype=np.float32)
+    assert bits_equal(oracle.appd(W2), W2)
+    n = 40
+    E = np.full((n, n), 7, dtype=np.uint32)
+    np.fill_diagonal(E, 0)
+    assert np.array_equal(oracle.appd(E), E)
+
+
+def test_two_separated_clusters():
+    # Two clusters far apart: every cross pair equals the smallest
+    # inter-cluster distance; within a cluster the answer is the cluster's own.
+    rng = np.random.default_rng(15)
+    a = rng.random((60, 2)).astype(np.float32)
+    b = (rng.random((50, 2)) + 100.0).astype(np.float32)
+    pts = np.vstack([a, b])
+    W = synth.euclid(pts)
+    M = oracle.appd(W)
+    cross = W[:60, 60:].min()
+    assert np.all(M[:60, 60:] == cross) and np.all(M[60:, :60] == cross)
+    assert bits_equal(M[:60, :60], oracle.appd(np.ascontiguousarray(W[:60, :60])))
+    assert bits_equal(M[60:, 60:], oracle.appd(np.ascontiguousarray(W[60:, 60:])))
+
+
+@pytest.mark.parametrize("which", ["gmm", "u32", "uniform01"])
+def test_invariants(which):
+    if which == "gmm":
+        W = synth.euclid(synth.gmm_points(120, 2, 5, sigma=0.5, seed=3, mean_box=10.0))
+    elif which == "u32":
+        W = synth.hash_u32(120, seed=5)
+    else:
+        W = synth.uniform01(120, seed=6)
+    n = W.shape[0]
+    M, cnt = oracle.appd(W, return_fill_count=True)
+    assert cnt == n * (n - 1)                       # each off-diagonal cell once
+    assert bits_equal(M, np.ascontiguousarray(M.T))  # symmetry
+    assert np.all(M.view(np.uint32).diagonal() == 0)
+    order, mst = oracle.prim(W)
+    lo = ((mst >> 16) & 0xFFFF).astype(np.int64)
+    hi = (mst & 0xFFFF).astype(np.int64)
+    mst_bits = set(W.view(np.uint32)[lo, hi].tolist())
+    off = ~np.eye(n, dtype=bool)
+    assert set(M.view(np.uint32)[off].tolist()) <= mst_bits  # every value is an MST weight
+    assert bits_equal(M[lo, hi], W[lo, hi])                 # MST edges are their own answer
+    KM, KW = keys_np(M), keys_np(W)
+    assert np.all(KM[off] <= KW[off])                        # M <= W
+    # ultrametric: M(i,k) <= max(M(i,j), M(j,k)) for all triples
+    lhs = KM[:, None, :]
+    rhs = np.maximum(KM[:, :, None], KM[None, :, :])
+    assert np.all(lhs <= rhs)
+    # histogram: each MST edge accounts for |tree1|*|tree2| pairs (Section 5),
+    # checked here as: count of pairs at each value == sum over MST edges of
+    # that weight of the product of the two side sizes when removed.
+    adj = {v: [] for v in range(n)}
+    for a, b in zip(lo.tolist(), hi.tolist()):
+        adj[a].append(b)
+        adj[b].append(a)
+    from collections import Counter
+    want = Counter()
+    for a, b, bits in zip(lo.tolist(), hi.tolist(), W.view(np.uint32)[lo, hi].tolist()):
+        # side of a after removing a-b, restricted to edges with larger-or-equal
+        # position in the strict order is not needed: Section 5 counts pairs
+        # whose tree path maximum is this edge.
+        code = (int(KW[a, b]) << 32) | (a << 16) | b
+        stack, seen = [a], {a}
+        while stack:
+            v = stack.pop()
+            for w in adj[v]:
+                if w in seen or {v, w} == {a, b}:
+                    continue
+                c = (int(KW[min(v, w), max(v, w)]) << 32) | (min(v, w) << 16) | max(v, w)
+                if c < code:
+                    seen.add(w)
+                    stack.append(w)
+        s1 = len(seen)
+        stack, seen2 = [b], {b}
+        while stack:
+            v = stack.pop()
+            for w in adj[v]:
+                if w in seen2 or {v, w} == {a, b}:
+                    continue
+                c = (int(KW[min(v, w), max(v, w)]) << 32) | (min(v, w) << 16) | max(v, w)
+                if c < code:
+                    seen2.add(w)
+                    stack.append(w)
+        want[bits] += 2 * s1 * len(seen2)
+    have = Counter(M.view(np.uint32)[off].tolist())
+    assert have == want
+    assert sum(want.values()) == n * (n - 1)
+
+
+def test_prim_order_identity():
+    # With Prim's order v_0..v_{n-1} and delta_k the weight that added v_k,
+    # M(v_a, v_b) = max_{a<k<=b} delta_k.  An independent second route to M.
+    for W in (synth.euclid(synth.uniform_points(300, 2, seed=21)), synth.hash_u32(257, seed=22)):
+        M = oracle.appd(W)
+        order, mst = oracle.prim(W)
+        n = W.shape[0]
+        dk = (mst >> 32).astype(np.uint64)
+        lo = ((mst >> 16) & 0xFFFF).astype(np.int64)
+        hi = (mst & 0xFFFF).astype(np.int64)
+        dbits = W.view(np.uint32)[lo, hi]
+        ref = np.zeros((n, n), dtype=np.uint32)
+        for a in range(n):
+            best_k, best_b = 0, 0
+            for b in range(a + 1, n):
+                if b == a + 1 or dk[b - 1] > best_k:
+                    best_k, best_b = dk[b - 1], dbits[b - 1]
+                ref[order[a], order[b]] = best_b
+                ref[order[b], order[a]] = best_b
+        assert np.array_equal(M.view(np.uint32), ref)
+
+
+def test_tree_rows_match_full_matrix():
+    W = synth.euclid(synth.gmm_points(400, 16, 8, sigma=1.0, seed=23, mean_std=5.0))
+    M = oracle.appd(W)
+    _, mst = oracle.prim(W)
+    src = [0, 5, 199, 399]
+    rows = oracle.tree_rows(W, mst, src)
+    assert bits_equal(rows, np.ascontiguousarray(M[src]))
+
+
+def test_special_values():
+    # NaN, infinities, signed zeros and negatives compare by totalOrder; the
+    # output keeps each selected weight's own bits.
+    rng = np.random.default_rng(24)
+    pool = np.array([0xFFC00000, 0xFF800000, 0xBF800000, 0x80000000, 0x00000000, 0x3F800000,
+                     0x7F800000, 0x7FC00000, 0x40000000, 0x7FC00001], dtype=np.uint32)
+    for n in (3, 5, 6):
+        for _ in range(5):
+            B = pool[rng.integers(0, len(pool), size=(n, n))]
+            B = np.triu(B, 1)
+            B = B + B.T
+            np.fill_diagonal(B, 0)
+            W = np.ascontiguousarray(B.astype(np.uint32)).view(np.float32)
+            ref = py_brute(W)
+            assert bits_equal(oracle.appd(W), ref)
+            assert bits_equal(oracle.fw(W), ref)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_planted_mistakes_are_caught(k):
+    rng = np.random.default_rng(25)
+    Ws = [sym_random(6, rng, np.float32, "uniform"), sym_random(30, rng, np.uint32, "uniform"),
+          synth.euclid(synth.uniform_points(40, 2, seed=26))]
+    refs = [threshold_connectivity(W) for W in Ws]
+    caught = False
+    with oracle.mutation(k):
+        for W, ref in zip(Ws, refs):
+            M, cnt = oracle.appd(W, return_fill_count=True)
+            n = W.shape[0]
+            if not bits_equal(M, ref) or cnt != n * (n - 1):
+                caught = True
+    assert caught, f"mutation {k} not caught by the pins"
+    # and the oracle is correct again afterwards
+    assert bits_equal(oracle.appd(Ws[0]), refs[0])
