@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark: all-pairs minimax-path (APPD) matrix on GB300.
+
+Default workload: one solve of a dense complete graph with n = 65536 vertices,
+W = FP32 Euclidean distances of 16-D points from a 32-component Gaussian
+mixture (means N(0, 25 I), sigma 1), seeded; W (17.2 GB) is generated on the
+device and stays resident; each step writes the 17.2 GB matrix M.
+
+Metric: APPD entries per second (n^2 / seconds per solve), whole job.
+Prints one JSON line (rank 0).  See the design doc for the byte counts.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload big|n16384|n16384u32|n1000]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "big": dict(n=65536, kind="gmm16", desc="single solve n=65536, FP32 Euclidean distances of "
+                                             "16-D points, 32-component Gaussian mixture"),
+    "n16384": dict(n=16384, kind="uniform2", desc="single solve n=16384, FP32 Euclidean "
+                                                   "distances of 2-D uniform points"),
+    "n16384u32": dict(n=16384, kind="u32", desc="single solve n=16384, uint32 weights uniform "
+                                                 "in [0, 2^16), heavy ties"),
+    "n1000": dict(n=1000, kind="gmm2", desc="single solve n=1000, FP32 Euclidean distances of "
+                                             "2-D points, 5-component Gaussian mixture"),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="big", choices=sorted(WORKLOADS))
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def points_for(kind: str, n: int, seed_shift: int = 0):
+    import synth
+    if kind == "gmm16":
+        return synth.gmm_points(n, 16, 32, sigma=1.0, seed=4 + seed_shift, mean_std=5.0)
+    if kind == "uniform2":
+        return synth.uniform_points(n, 2, seed=2 + seed_shift)
+    if kind == "gmm2":
+        return synth.gmm_points(n, 2, 5, sigma=0.5, seed=1 + seed_shift, mean_box=10.0)
+    return None
+
+
+def host_matrix(kind: str, n: int):
+    import synth
+    if kind == "u32":
+        return synth.hash_u32(n, seed=3)
+    return synth.euclid(points_for(kind, n))
+
+
+# ------------------------------------------------------------ measurement
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None if there is none or the kernel's source changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d[kernel]
+        src = os.path.join(ROOT, ent["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != ent["source_sha256_16"]:
+            return None
+        return ent["bytes_per_launch_full"]
+    except Exception:
+        return None
+
+
+def cpu_baseline(kind: str, n_full: int, budget_s: float = 12.0):
+    """The oracle (Prim + Algorithm 4, single thread) on a bounded sample of the
+    same workload: a smaller graph from the same distribution."""
+    import oracle
+    import synth
+    n = min(n_full, 16384 if kind != "u32" else 16384)
+    if kind == "u32":
+        W = synth.hash_u32(n, seed=3)
+    else:
+        W = synth.euclid(points_for(kind, n))
+    runs, total = 0, 0.0
+    while runs < 3 and (total < budget_s or runs == 0):
+        t0 = time.perf_counter()
+        oracle.appd(W)
+        total += time.perf_counter() - t0
+        runs += 1
+    return {"value": runs * n * n / total, "unit": "entries/s", "cores": 1, "kind": "oracle",
+            "sample": f"n={n} graph from the same distribution, {runs} run(s), "
+                      f"{total:.1f} s total, Prim + Algorithm 4, one thread"}
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    import oracle
+    import synth
+    n = min(wl["n"], 8192)
+    if wl["kind"] == "u32":
+        W = synth.hash_u32(n, seed=3)
+    else:
+        W = synth.euclid(points_for(wl["kind"], n))
+    for _ in range(args.warmup):
+        oracle.appd(W)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.appd(W)
+    dt = time.perf_counter() - t0
+    value = args.steps * n * n / dt
+    line = {
+        "impl": "reference", "metric": "APPD entries/s", "value": value, "unit": "entries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "n": wl["n"], "sample_n": n},
+        "cpu_baseline": {"value": value, "unit": "entries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: the oracle on an n={n} graph from the same "
+                                   "distribution (Prim + Algorithm 4, one thread)"},
+        "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2407_07058_gb300 import appd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = WORKLOADS[args.workload]
+    n, kind = wl["n"], wl["kind"]
+    stream = torch.cuda.current_stream()
+    # ---- inputs resident on the device
+    if kind == "u32":
+        W = torch.empty((n, n), dtype=torch.int32, device=dev)
+        synth.device_hash_u32(3, n, W.data_ptr(), stream.cuda_stream)
+    else:
+        pts = torch.from_numpy(points_for(kind, n)).to(dev)
+        W = torch.empty((n, n), dtype=torch.float32, device=dev)
+        synth.device_euclid(pts.data_ptr(), n, pts.shape[1], W.data_ptr(), stream.cuda_stream)
+        del pts
+    M = torch.empty_like(W)
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        appd.solve(W, out=M)
+    torch.cuda.synchronize()
+    if appd.last_device_status() != 0:
+        raise RuntimeError("device status error during warm-up")
+
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        appd.profile_begin()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            appd.solve(W, out=M)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        prof = appd.profile_end()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if appd.last_device_status() != 0:
+        raise RuntimeError("device status error in the timed region")
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * args.steps * n * n / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (algorithmic bytes per launch)
+    peak, peak_src = measured_peaks()
+    c1 = prof["c1"]
+    cand = {
+        "k_fill": (prof["fill"], 4.0 * n * n),
+        "k_contract(W)": (prof["contract_w"], 4.0 * n * n + 8.0 * c1 * c1),
+        "k_rowmin": (prof["rowmin"], 4.0 * n * n),
+    }
+    dom = max(cand, key=lambda k: cand[k][0])
+    dom_ms = cand[dom][0] / args.steps
+    achieved = cand[dom][1] / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": ncu_traffic(dom),
+                "algorithmic_bytes_per_launch": cand[dom][1], "ms_per_launch": dom_ms}
+    design_bytes = (28.0 / 3.0) * n * n
+    solve_frac = design_bytes / (ms_step / 1e3) / 1e9 / peak
+
+    # ---- end to end through the host entry point (pinned buffers)
+    e2e = None
+    if not args.no_e2e:
+        Wh = torch.empty((n, n), dtype=W.dtype, pin_memory=True)
+        Wh.copy_(W)
+        Mh = torch.empty((n, n), dtype=W.dtype, pin_memory=True)
+        dt_code = appd.F32 if W.dtype == torch.float32 else appd.U32
+        appd.solve_host_ptr(Wh.data_ptr(), n, dt_code, Mh.data_ptr())   # warm staging
+        barrier()
+        ke = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            appd.solve_host_ptr(Wh.data_ptr(), n, dt_code, Mh.data_ptr())
+        te = time.perf_counter() - t0
+        barrier()
+        e2e = {"value": world * ke * n * n / te, "unit": "entries/s",
+               "h2d_bytes_per_step": 4 * n * n, "d2h_bytes_per_step": 4 * n * n,
+               "steps": ke, "ms_per_step": 1e3 * te / ke}
+        del Wh, Mh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(kind, n)
+
+    if rank == 0:
+        line = {
+            "metric": "APPD entries/s", "value": value, "unit": "entries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (W and M 4n^2 bytes each)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": prof["launches"],
+            "clocks": clk.summary(),
+            "phases_ms_per_step": {k: prof[k] / args.steps for k in appd.PHASES},
+            "c1": c1,
+            "hbm_frac_solve_design_bytes": solve_frac,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

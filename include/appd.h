@@ -1,0 +1,221 @@
+/*
+ * appd.h -- C ABI of the GB300 all-pairs minimax-path (APPD) library.
+ *
+ * Problem (arxiv 2407.07058, Section 1, Eq. 1-2): for a dense undirected
+ * complete graph with symmetric n x n weight matrix W, compute the n x n
+ * matrix M with M(i,j) = min over all i-j paths p of the largest edge weight
+ * on p (the minimax / longest-leg / MMJ distance; the matrix is the "all
+ * points path distance", APPD).  The paper computes it with Prim's MST and
+ * Algorithm 4 (Sections 3 and 5); this library computes the same matrix on
+ * one GPU with a dense Boruvka MST, a single-linkage leaf order and a tiled
+ * range-maximum fill.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are dense, row-major, n*n elements of 4 bytes.  dtype APPD_F32:
+ *    IEEE-754 binary32; APPD_U32: unsigned 32-bit integers.
+ *  - Ordering: U32 weights compare as unsigned integers; F32 weights compare
+ *    by IEEE-754 totalOrder (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN).
+ *    Ties are broken by the edge's endpoint pair, so results never depend on
+ *    tie-breaking (Section 5 notes ties do not matter).
+ *  - Output: every off-diagonal M(i,j) is the bit pattern of one input weight
+ *    (the largest edge on a minimax path); the diagonal M(i,i) is all-zero
+ *    bits.  W(i,i) is never read.  Results are exact (bit-identical to the
+ *    definition), so there is no tolerance.
+ *  - W must be symmetric (undirected graph, Section 1).  Only the upper
+ *    triangle is relied on by the specification; results for an asymmetric W
+ *    are unspecified.  appd_check_symmetric validates.
+ *  - 1 <= n <= 65536 (edge endpoints are packed in 16 bits); n == 0 is a
+ *    no-op that returns APPD_OK; n > 65536 returns APPD_ERR_TOO_LARGE.
+ *  - Device pointers are owned by the caller.  Calls are asynchronous on the
+ *    given CUDA stream (cudaStream_t, passed as appd_stream_t; NULL is the
+ *    legacy default stream).  Argument errors are returned synchronously
+ *    before anything is enqueued.  Errors detected on the device (a bounded
+ *    wait that ran out, an internal consistency check) are recorded in a
+ *    per-device status word that appd_last_device_status returns after the
+ *    caller synchronizes the stream.
+ *  - The library keeps a workspace per (device, n) that it allocates on first
+ *    use and reuses; calls that share a workspace must be ordered (one stream,
+ *    or synchronized).  appd_release_workspaces frees them.
+ *  - M is also used as scratch space during a solve (its contents before the
+ *    call are ignored).  M == W (in place) is allowed; a partial overlap of
+ *    M and W returns APPD_ERR_ALIAS.
+ */
+#ifndef APPD_H
+#define APPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle (cudaStream_t); declared opaquely so that this header
+ * does not require the CUDA headers. */
+typedef struct CUstream_st *appd_stream_t;
+
+typedef enum { APPD_F32 = 0, APPD_U32 = 1 } appd_dtype;
+
+typedef enum {
+    APPD_OK = 0,
+    APPD_ERR_INVALID = 1,    /* null pointer, n < 0, bad dtype, bad batch layout */
+    APPD_ERR_TOO_LARGE = 2,  /* n > 65536 */
+    APPD_ERR_NOMEM = 3,      /* device or host allocation failed */
+    APPD_ERR_CUDA = 4,       /* a CUDA runtime call failed */
+    APPD_ERR_ASYMMETRIC = 5, /* appd_check_symmetric found W(i,j) != W(j,i) */
+    APPD_ERR_TIMEOUT = 6,    /* a bounded device wait ran out */
+    APPD_ERR_BUSY = 7,       /* server: admission refused (budget or slots) */
+    APPD_ERR_ALIAS = 8,      /* M partially overlaps W */
+    APPD_ERR_NOT_FOUND = 9,  /* server: unknown request id */
+    APPD_ERR_INTERNAL = 10   /* an internal consistency check failed on the device */
+} appd_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *appd_status_str(appd_status st);
+
+/*
+ * appd_solve -- the APPD matrix of one graph (Eq. 1-2).
+ *   W   device pointer, n*n elements of dtype dt, row-major, symmetric.
+ *   n   number of vertices.
+ *   dt  APPD_F32 or APPD_U32.
+ *   M   device pointer, n*n elements of dtype dt, receives the result.
+ *   s   CUDA stream.
+ * Pipeline (all on the GPU, no host synchronisation): dense Boruvka MST by
+ * row minima and block-min contraction of W (the MST step of Section 3, which
+ * the paper does with Prim), a single-linkage leaf order of the MST with the
+ * merge heights between neighbours (the ascending form of Section 3), and a
+ * tiled fill M(i,j) = largest merge height between the two leaves.
+ */
+appd_status appd_solve(const void *W, int64_t n, appd_dtype dt, void *M, appd_stream_t s);
+
+/*
+ * appd_solve_alg4 -- same result as appd_solve, but M is written by a GPU
+ * form of Algorithm 4's calculation-and-copy step (Sections 3, 5 and the
+ * parallel variant of Section 6.2): one work item per MST edge e fills the
+ * cross block tree1 x tree2 (and its transpose) with w(e).  Kept to compare
+ * the paper's fill pattern with the tiled fill.  Arguments as appd_solve.
+ */
+appd_status appd_solve_alg4(const void *W, int64_t n, appd_dtype dt, void *M, appd_stream_t s);
+
+/*
+ * appd_solve_host -- appd_solve on host memory: copies W (host, n*n) to the
+ * device, solves, and copies M back to host memory M_host, all on stream s.
+ * Host buffers may be pageable or pinned; the call returns after M_host holds
+ * the result (it synchronizes s).  Device staging buffers are kept with the
+ * workspace.
+ */
+appd_status appd_solve_host(const void *W_host, int64_t n, appd_dtype dt, void *M_host,
+                            appd_stream_t s);
+
+/*
+ * appd_mst -- the minimum spanning tree computed by the solve's MST stage.
+ *   edges_out  device pointer to n-1 uint64 values; each is
+ *              key << 32 | lo << 16 | hi, where lo < hi are the endpoints and
+ *              key is the order key of W(lo,hi) (the weight's bits for U32;
+ *              for F32, bits | 0x80000000 if the sign bit is clear, else ~bits).
+ *              Edge order in the array is unspecified.
+ * Under the strict order (key, lo, hi) the MST is unique, so the edge set can
+ * be compared exactly with any correct MST algorithm (Section 3 uses Prim).
+ */
+appd_status appd_mst(const void *W, int64_t n, appd_dtype dt, uint64_t *edges_out,
+                     appd_stream_t s);
+
+/*
+ * appd_leaf_order -- the single-linkage leaf order used by the fill.
+ *   pos_out  device, n uint32: position of vertex v in the order.
+ *   gap_out  device, n-1 uint32: gap_out[k] = order key of the largest edge
+ *            on the MST path between the vertices at positions k and k+1.
+ * For all i != j: key(M(i,j)) = max(gap_out[min(p_i,p_j) .. max(p_i,p_j)-1]).
+ * (Reading off distances from the dendrogram, Section 7.)
+ */
+appd_status appd_leaf_order(const void *W, int64_t n, appd_dtype dt, uint32_t *pos_out,
+                            uint32_t *gap_out, appd_stream_t s);
+
+/*
+ * appd_solve_batched -- many independent graphs in one launch sequence.
+ *   offsets  host array, count entries: element offset of graph g in Ws and Ms.
+ *   Ws       device base pointer; graph g's W starts at (elem*)Ws + offsets[g].
+ *   ns       host array, count entries: n of each graph (1..65536).
+ *   dts      host array of count bytes (APPD_F32 / APPD_U32) or NULL (all F32).
+ *   Ms       device base pointer; graph g's M starts at (elem*)Ms + offsets[g].
+ *   count    number of graphs.
+ * The ranges [offsets[g], offsets[g] + ns[g]^2) must not overlap between
+ * graphs and M ranges must not overlap W ranges except exactly (in place).
+ * Graphs up to a size cut-over run one per CTA inside a persistent kernel
+ * with a work queue; larger graphs use the single-solve pipeline.
+ */
+appd_status appd_solve_batched(const int64_t *offsets, const void *Ws, const int64_t *ns,
+                               const uint8_t *dts, void *Ms, int32_t count, appd_stream_t s);
+
+/*
+ * appd_check_symmetric -- returns APPD_OK if W(i,j) and W(j,i) have identical
+ * bits for all i < j, APPD_ERR_ASYMMETRIC otherwise.  Synchronizes s.
+ */
+appd_status appd_check_symmetric(const void *W, int64_t n, appd_dtype dt, appd_stream_t s);
+
+/*
+ * appd_last_device_status -- synchronizes s, then returns and clears the
+ * device-detected error status of the current device (APPD_OK,
+ * APPD_ERR_TIMEOUT or APPD_ERR_INTERNAL).
+ */
+appd_status appd_last_device_status(appd_stream_t s);
+
+/* Frees every cached workspace on the current device (synchronizes it). */
+appd_status appd_release_workspaces(void);
+
+/* ----------------------------------------------------------- profiling */
+/*
+ * appd_profile_begin -- from now on the library records a CUDA event pair on
+ * the caller's stream around each group of its kernel launches and counts
+ * the kernels it launches.  Returns 0.
+ * appd_profile_end -- synchronizes the device, stops recording, and writes
+ * up to cap doubles to out: summed device milliseconds per phase
+ *   [0] round-1 row minima   [1] Boruvka steps       [2] contraction of W
+ *   [3] later contractions   [4] leaf order          [5] fill of M
+ * then [6] kernels launched, [7] components after round 1 of the last solve.
+ * Returns the number of values written.
+ */
+int32_t appd_profile_begin(void);
+int32_t appd_profile_end(double *out, int32_t cap);
+
+/* ------------------------------------------------------------- serving */
+/*
+ * A continuous-batching solve server on one GPU.  Requests of different n
+ * are admitted while the sum of their device footprints stays within an HBM
+ * budget; each admitted request owns a slot holding its W and M on the
+ * device.  Committed requests are batched into the persistent batched kernel
+ * as they arrive, so new work starts while earlier work is still running.
+ */
+typedef struct appd_server appd_server;
+
+/* budget_bytes: device bytes the server may hold (slots + workspace).
+ * max_inflight: upper bound on admitted, unreleased requests. */
+appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_server **out);
+
+/* Admit a request for an n-vertex graph of dtype dt.  On APPD_OK, *req_id is
+ * its id and *W_slot a device pointer to n*n elements that the caller fills
+ * (on any stream, synchronized before commit) and must not touch after
+ * commit.  Returns APPD_ERR_BUSY if the budget or slot count is exhausted. */
+appd_status appd_server_submit(appd_server *sv, int64_t n, appd_dtype dt, uint64_t *req_id,
+                               void **W_slot);
+
+/* Queue an admitted request for solving. */
+appd_status appd_server_commit(appd_server *sv, uint64_t req_id);
+
+/* Collect finished requests: up to cap ids in done_ids and their device M
+ * pointers in M_ptrs (valid until release); *n_done receives the count.
+ * Never blocks. */
+appd_status appd_server_poll(appd_server *sv, uint64_t *done_ids, const void **M_ptrs,
+                             int32_t cap, int32_t *n_done);
+
+/* Free a finished request's slot (its M pointer becomes invalid). */
+appd_status appd_server_release(appd_server *sv, uint64_t req_id);
+
+/* Wait for in-flight work, free all slots and the server. */
+appd_status appd_server_destroy(appd_server *sv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APPD_H */

@@ -1,0 +1,263 @@
+"""Python binding of the APPD C ABI (include/appd.h).
+
+Argument marshalling only: every step of a solve runs in the CUDA library
+``_build/libappd.so``.  Tensors must live on a CUDA device; there is no CPU
+fallback, and loading fails loudly if the library cannot be built or loaded.
+
+dtype mapping: ``torch.float32`` -> APPD_F32; ``torch.int32`` / ``torch.uint32``
+-> APPD_U32 (the 32 bits are read as an unsigned integer).
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import _build
+
+F32, U32 = 0, 1
+STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD_ERR_NOMEM",
+          4: "APPD_ERR_CUDA", 5: "APPD_ERR_ASYMMETRIC", 6: "APPD_ERR_TIMEOUT", 7: "APPD_ERR_BUSY",
+          8: "APPD_ERR_ALIAS", 9: "APPD_ERR_NOT_FOUND", 10: "APPD_ERR_INTERNAL"}
+
+# every symbol that include/appd.h declares
+EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host", "appd_mst",
+           "appd_leaf_order", "appd_solve_batched", "appd_check_symmetric",
+           "appd_last_device_status", "appd_release_workspaces", "appd_profile_begin",
+           "appd_profile_end", "appd_server_create",
+           "appd_server_submit", "appd_server_commit", "appd_server_poll", "appd_server_release",
+           "appd_server_destroy"]
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+class AppdError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+def load(build_if_missing: bool = True):
+    """Load libappd.so (building it first if it is missing or stale)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        if build_if_missing and _build.is_stale():
+            _build.build()
+        lib = ctypes.CDLL(_build.lib_path())
+        vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+        ci = ctypes.c_int
+        sig = {
+            "appd_solve": [vp, i64, ci, vp, vp],
+            "appd_solve_alg4": [vp, i64, ci, vp, vp],
+            "appd_solve_host": [vp, i64, ci, vp, vp],
+            "appd_mst": [vp, i64, ci, vp, vp],
+            "appd_leaf_order": [vp, i64, ci, vp, vp, vp],
+            "appd_solve_batched": [vp, vp, vp, vp, vp, i32, vp],
+            "appd_check_symmetric": [vp, i64, ci, vp],
+            "appd_last_device_status": [vp],
+            "appd_release_workspaces": [],
+            "appd_server_create": [ctypes.c_size_t, i32, ctypes.POINTER(vp)],
+            "appd_server_submit": [vp, i64, ci, ctypes.POINTER(u64), ctypes.POINTER(vp)],
+            "appd_server_commit": [vp, u64],
+            "appd_server_poll": [vp, vp, vp, i32, ctypes.POINTER(i32)],
+            "appd_server_release": [vp, u64],
+            "appd_server_destroy": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ci
+        lib.appd_profile_begin.argtypes = []
+        lib.appd_profile_begin.restype = i32
+        lib.appd_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), i32]
+        lib.appd_profile_end.restype = i32
+        lib.appd_status_str.argtypes = [ci]
+        lib.appd_status_str.restype = ctypes.c_char_p
+        _LIB = lib
+        return lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise AppdError(code, what)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        return U32
+    raise TypeError(f"unsupported dtype {t.dtype}: use float32, int32 or uint32")
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _square_cuda(W):
+    if not W.is_cuda:
+        raise ValueError("W must be a CUDA tensor (no CPU path)")
+    if W.dim() != 2 or W.shape[0] != W.shape[1] or not W.is_contiguous():
+        raise ValueError("W must be a contiguous square matrix")
+    return W.shape[0]
+
+
+def solve(W, out=None, stream=None, alg4: bool = False):
+    """APPD matrix of W (n x n, symmetric) on W's device; returns M (same dtype)."""
+    import torch
+    n = _square_cuda(W)
+    dt = _dtype_code(W)
+    M = torch.empty_like(W) if out is None else out
+    fn = load().appd_solve_alg4 if alg4 else load().appd_solve
+    with torch.cuda.device(W.device):
+        _check(fn(W.data_ptr(), n, dt, M.data_ptr(), _stream_ptr(stream)), "appd_solve")
+    return M
+
+
+def solve_alg4(W, out=None, stream=None):
+    return solve(W, out=out, stream=stream, alg4=True)
+
+
+def solve_host(W: np.ndarray, stream=None) -> np.ndarray:
+    """APPD of a host matrix through appd_solve_host (copies inside the call)."""
+    Wc = np.ascontiguousarray(W)
+    if Wc.dtype == np.float32:
+        dt = F32
+    elif Wc.dtype in (np.uint32, np.int32):
+        dt = U32
+    else:
+        raise TypeError(f"unsupported dtype {Wc.dtype}")
+    M = np.empty_like(Wc)
+    _check(load().appd_solve_host(Wc.ctypes.data, Wc.shape[0], dt, M.ctypes.data,
+                                  _stream_ptr(stream)), "appd_solve_host")
+    return M
+
+
+def solve_host_ptr(W_ptr: int, n: int, dt: int, M_ptr: int, stream=None):
+    """appd_solve_host on raw host pointers (e.g. pinned buffers)."""
+    _check(load().appd_solve_host(W_ptr, n, dt, M_ptr, _stream_ptr(stream)), "appd_solve_host")
+
+
+def mst(W, stream=None):
+    """The n-1 MST edges as int64 values key<<32 | lo<<16 | hi (order unspecified)."""
+    import torch
+    n = _square_cuda(W)
+    E = torch.empty(max(n - 1, 1), dtype=torch.int64, device=W.device)
+    with torch.cuda.device(W.device):
+        _check(load().appd_mst(W.data_ptr(), n, _dtype_code(W), E.data_ptr(), _stream_ptr(stream)),
+               "appd_mst")
+    return E[: n - 1]
+
+
+def leaf_order(W, stream=None):
+    """(pos, gap): leaf position of each vertex and the n-1 merge-height keys."""
+    import torch
+    n = _square_cuda(W)
+    pos = torch.empty(n, dtype=torch.int32, device=W.device)
+    gap = torch.empty(max(n - 1, 1), dtype=torch.int32, device=W.device)
+    with torch.cuda.device(W.device):
+        _check(load().appd_leaf_order(W.data_ptr(), n, _dtype_code(W), pos.data_ptr(),
+                                      gap.data_ptr(), _stream_ptr(stream)), "appd_leaf_order")
+    return pos, gap[: n - 1]
+
+
+def solve_batched(Wflat, offsets, ns, dts=None, out=None, stream=None):
+    """Many graphs: graph g is Wflat[offsets[g] : offsets[g] + ns[g]**2] (row-major)."""
+    import torch
+    if not Wflat.is_cuda:
+        raise ValueError("Wflat must be a CUDA tensor")
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nn = np.ascontiguousarray(np.asarray(ns, dtype=np.int64))
+    dd = None if dts is None else np.ascontiguousarray(np.asarray(dts, dtype=np.uint8))
+    M = torch.empty_like(Wflat) if out is None else out
+    with torch.cuda.device(Wflat.device):
+        _check(load().appd_solve_batched(off.ctypes.data, Wflat.data_ptr(), nn.ctypes.data,
+                                         None if dd is None else dd.ctypes.data, M.data_ptr(),
+                                         len(nn), _stream_ptr(stream)), "appd_solve_batched")
+    return M
+
+
+def check_symmetric(W, stream=None) -> bool:
+    n = _square_cuda(W)
+    code = load().appd_check_symmetric(W.data_ptr(), n, _dtype_code(W), _stream_ptr(stream))
+    if code == 5:
+        return False
+    _check(code, "appd_check_symmetric")
+    return True
+
+
+def last_device_status(stream=None) -> int:
+    return int(load().appd_last_device_status(_stream_ptr(stream)))
+
+
+PHASES = ["rowmin", "boruvka_step", "contract_w", "contract_c", "leaf_order", "fill"]
+
+
+def profile_begin():
+    load().appd_profile_begin()
+
+
+def profile_end() -> dict:
+    """Per-phase device ms since profile_begin, kernel launch count, c1."""
+    buf = (ctypes.c_double * 8)()
+    k = load().appd_profile_end(buf, 8)
+    vals = [buf[i] for i in range(k)]
+    out = {name: vals[i] for i, name in enumerate(PHASES)}
+    out["launches"] = int(vals[6])
+    out["c1"] = int(vals[7])
+    return out
+
+
+def release_workspaces():
+    _check(load().appd_release_workspaces(), "appd_release_workspaces")
+
+
+class Server:
+    """Continuous-batching solve server (appd_server_* entry points)."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 4096):
+        self._h = ctypes.c_void_p()
+        _check(load().appd_server_create(budget_bytes, max_inflight, ctypes.byref(self._h)),
+               "appd_server_create")
+
+    def submit(self, n: int, dt: int):
+        """Returns (req_id, W_slot_ptr) or None when admission is refused (busy)."""
+        rid = ctypes.c_uint64()
+        slot = ctypes.c_void_p()
+        code = load().appd_server_submit(self._h, n, dt, ctypes.byref(rid), ctypes.byref(slot))
+        if code == 7:
+            return None
+        _check(code, "appd_server_submit")
+        return rid.value, slot.value
+
+    def commit(self, rid: int):
+        _check(load().appd_server_commit(self._h, rid), "appd_server_commit")
+
+    def poll(self, cap: int = 1024):
+        ids = (ctypes.c_uint64 * cap)()
+        ptrs = (ctypes.c_void_p * cap)()
+        k = ctypes.c_int32()
+        _check(load().appd_server_poll(self._h, ids, ptrs, cap, ctypes.byref(k)), "appd_server_poll")
+        return [(ids[i], ptrs[i]) for i in range(k.value)]
+
+    def release(self, rid: int):
+        _check(load().appd_server_release(self._h, rid), "appd_server_release")
+
+    def close(self):
+        if self._h:
+            _check(load().appd_server_destroy(self._h), "appd_server_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

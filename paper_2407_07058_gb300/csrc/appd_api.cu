@@ -1,0 +1,586 @@
+// appd_api.cu -- the C ABI (include/appd.h): argument checks, the per-device
+// workspace, the device status word, and the launch sequence of a solve.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/appd.h"
+#include "internal.h"
+
+using namespace appd;
+
+namespace {
+
+constexpr int MAX_DEV = 64;
+std::mutex g_mu;
+Workspace* g_ws[MAX_DEV] = {};
+u32* g_status[MAX_DEV] = {};
+
+// ------------------------------------------------------------- profiling
+struct ProfMark {
+    int phase;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfMark> g_marks;
+std::vector<cudaEvent_t> g_event_pool;
+size_t g_pool_used = 0;
+long long g_launches = 0;
+Counters* g_last_ctr = nullptr;
+
+cudaEvent_t pool_event()
+{
+    if (g_pool_used == g_event_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        g_event_pool.push_back(e);
+    }
+    return g_event_pool[g_pool_used++];
+}
+
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+appd_status cuda_fail(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return APPD_ERR_NOMEM;
+    return APPD_ERR_CUDA;
+}
+
+// Carves the workspace arrays for capacity `cap` out of one allocation (or
+// only measures when base == nullptr).
+size_t carve(Workspace& w, char* base, int64_t cap)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = align_up(off, 256);
+        char* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const size_t N = (size_t)cap;
+    const int lv = ceil_log2(cap) + 1;
+    const size_t ntiles = (N + 2047) / 2048 + 1;
+    w.ctr = (Counters*)take(sizeof(Counters));
+    w.part = (u32*)take(4096 * sizeof(u32));
+    w.best[0] = (u64*)take(N * 8);
+    w.best[1] = (u64*)take(N * 8);
+    u32** u32s[] = {&w.comp, &w.hook, &w.par, &w.flag, &w.rootid, &w.label, &w.cnt, &w.fillc,
+                    &w.members, &w.nchunk, &w.item_group, &w.deg, &w.afill, &w.parent, &w.pe_key,
+                    &w.nha, &w.first_child, &w.next_sib, &w.pos, &w.order, &w.nsize, &w.gap};
+    for (u32** p : u32s)
+        *p = (u32*)take((N + 4) * sizeof(u32));
+    w.gstart = (u32*)take((N + 4) * sizeof(u32));
+    w.chunk_start = (u32*)take((N + 4) * sizeof(u32));
+    w.adj_off = (u32*)take((N + 4) * sizeof(u32));
+    w.a4_start = (u32*)take((N + 4) * sizeof(u32));
+    w.mst = (u64*)take((N + 1) * 8);
+    w.adj = (u32*)take(2 * N * sizeof(u32));
+    w.aslot = (u32*)take(2 * N * sizeof(u32));
+    for (int i = 0; i < 2; ++i) {
+        w.lr_d[i] = (u32*)take(2 * N * sizeof(u32) + 16);
+        w.lr_nx[i] = (u32*)take(2 * N * sizeof(u32) + 16);
+        w.skey[i] = (u64*)take((N + 1) * 8);
+    }
+    w.ord = (u64*)take(N * 8);
+    w.jump = (u32*)take((size_t)lv * N * sizeof(u32));
+    w.mxo = (u64*)take((size_t)lv * N * 8);
+    w.hist = (u32*)take(256 * ntiles * sizeof(u32));
+    w.st = (u32*)take((size_t)lv * N * sizeof(u32));
+    return align_up(off, 256);
+}
+
+// The device's workspace with capacity >= n (grown if needed).
+appd_status get_ws(int64_t n, Workspace** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return APPD_ERR_CUDA;
+    Workspace*& w = g_ws[dev];
+    if (w && w->cap >= n) {
+        *out = w;
+        return APPD_OK;
+    }
+    int64_t cap = 1024;
+    while (cap < n)
+        cap *= 2;
+    if (cap > 65536)
+        cap = 65536;
+    Workspace* nw = new Workspace();
+    nw->device = dev;
+    nw->cap = cap;
+    nw->n = 0;
+    size_t bytes = carve(*nw, nullptr, cap);
+    void* base = nullptr;
+    if (w) {
+        cudaDeviceSynchronize();
+        cudaFree(w->base);
+        cudaFree(w->cscratch);
+        cudaFree(w->hostW);
+        cudaFree(w->hostM);
+        delete w;
+        w = nullptr;
+    }
+    e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) {
+        delete nw;
+        return cuda_fail(e);
+    }
+    carve(*nw, (char*)base, cap);
+    nw->base = base;
+    nw->bytes = bytes;
+    cudaDeviceGetAttribute(&nw->sms, cudaDevAttrMultiProcessorCount, dev);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    nw->coop_blocks = nw->sms;
+    nw->coop_threads = 512;
+    nw->contract_blocks = nw->sms;
+    nw->bin_cap = (u32)((smem_optin - 2048) / 8);
+    w = nw;
+    *out = w;
+    return APPD_OK;
+}
+
+appd_status get_status(u32** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return APPD_ERR_CUDA;
+    if (!g_status[dev]) {
+        cudaError_t e = cudaMalloc(&g_status[dev], 256);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        e = cudaMemset(g_status[dev], 0, 256);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+    }
+    *out = g_status[dev];
+    return APPD_OK;
+}
+
+// Per-solve sizes on the shared workspace.
+void set_sizes(Workspace& w, int64_t n)
+{
+    w.n = n;
+    w.levels = n > 1 ? ceil_log2(n) : 1;
+    if (w.levels < 1)
+        w.levels = 1;
+    int stl = 1;
+    while (((int64_t)1 << stl) <= n - 1)
+        ++stl;
+    w.st_levels = stl;
+    w.ntiles = (u32)((n - 1 + 2047) / 2048);
+    if (w.ntiles == 0)
+        w.ntiles = 1;
+}
+
+appd_status check_args(const void* W, int64_t n, int dt, const void* M)
+{
+    if (n < 0 || !W || !M || (dt != APPD_F32 && dt != APPD_U32))
+        return APPD_ERR_INVALID;
+    if (n > 65536)
+        return APPD_ERR_TOO_LARGE;
+    if (M != W) {
+        const char* a = (const char*)W;
+        const char* b = (const char*)M;
+        size_t bytes = (size_t)n * (size_t)n * 4;
+        if (a < b + bytes && b < a + bytes)
+            return APPD_ERR_ALIAS;
+    }
+    return APPD_OK;
+}
+
+// Holds the workspace of one solve; n is recorded in the workspace's size
+// fields for the launch functions.
+struct SolveCtx {
+    Workspace* ws = nullptr;
+    u32* status = nullptr;
+    int64_t cap = 0;
+};
+
+appd_status prepare(int64_t n, SolveCtx& c)
+{
+    appd_status st = get_ws(n, &c.ws);
+    if (st != APPD_OK)
+        return st;
+    st = get_status(&c.status);
+    if (st != APPD_OK)
+        return st;
+    c.cap = c.ws->cap;
+    return APPD_OK;
+}
+
+// Runs MST + leaf order for a graph of size n on the workspace (whose arrays
+// have capacity c.cap).  cbuf must hold contraction_scratch_bytes(n).
+appd_status mst_and_order(SolveCtx& c, const void* W, int64_t n, int dt, void* cbuf, bool order,
+                          cudaStream_t s)
+{
+    Workspace& w = *c.ws;
+    set_sizes(w, n);
+    g_last_ctr = w.ctr;
+    cudaError_t e = run_mst(w, W, dt, cbuf, contraction_scratch_bytes(n), c.status, s);
+    if (e == cudaSuccess && order) {
+        prof_begin(PH_LEAF, s);
+        e = run_leaf_order(w, c.status, s);
+        prof_end(PH_LEAF, s);
+        prof_launches(1);
+    }
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
+appd_status ensure_cscratch(Workspace& w, int64_t n)
+{
+    size_t need = contraction_scratch_bytes(n);
+    if (w.cscratch_bytes >= need)
+        return APPD_OK;
+    cudaDeviceSynchronize();
+    cudaFree(w.cscratch);
+    w.cscratch = nullptr;
+    w.cscratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&w.cscratch, need);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    w.cscratch_bytes = need;
+    return APPD_OK;
+}
+
+appd_status solve_impl(const void* W, int64_t n, int dt, void* M, cudaStream_t s, bool alg4)
+{
+    appd_status st = check_args(W, n, dt, M);
+    if (st != APPD_OK || n == 0)
+        return st;
+    std::lock_guard<std::mutex> lk(g_mu);
+    SolveCtx c;
+    if ((st = prepare(n, c)) != APPD_OK)
+        return st;
+    Workspace& w = *c.ws;
+    void* cbuf = M;
+    if (M == W) {
+        if ((st = ensure_cscratch(w, n)) != APPD_OK)
+            return st;
+        cbuf = w.cscratch;
+    }
+    if ((st = mst_and_order(c, W, n, dt, cbuf, true, s)) != APPD_OK)
+        return st;
+    set_sizes(w, n);
+    prof_begin(PH_FILL, s);
+    cudaError_t e = alg4 ? run_fill_alg4(w, dt, M, c.status, s) : run_fill(w, dt, M, s);
+    prof_end(PH_FILL, s);
+    prof_launches(alg4 ? 4 : 1);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
+__global__ void k_check_sym(const u32* __restrict__ W, u32 n, u32* __restrict__ bad)
+{
+    u64 total = (u64)n * n;
+    for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (u64)gridDim.x * blockDim.x) {
+        u32 i = (u32)(idx / n), j = (u32)(idx - (u64)i * n);
+        if (i < j && W[idx] != W[(size_t)j * n + i])
+            *bad = 1u;
+    }
+}
+
+}  // namespace
+
+namespace appd {
+
+void prof_begin(int phase, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on)
+        return;
+    ProfMark m{phase, pool_event(), nullptr};
+    cudaEventRecord(m.a, s);
+    g_marks.push_back(m);
+}
+
+void prof_end(int phase, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on)
+        return;
+    for (auto it = g_marks.rbegin(); it != g_marks.rend(); ++it) {
+        if (it->phase == phase && it->b == nullptr) {
+            it->b = pool_event();
+            cudaEventRecord(it->b, s);
+            return;
+        }
+    }
+}
+
+void prof_launches(int k)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_on)
+        g_launches += k;
+}
+
+}  // namespace appd
+
+extern "C" {
+
+int32_t appd_profile_begin(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_marks.clear();
+    g_pool_used = 0;
+    g_launches = 0;
+    g_prof_on = true;
+    return 0;
+}
+
+int32_t appd_profile_end(double* out, int32_t cap)
+{
+    cudaDeviceSynchronize();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = false;
+    double acc[PH_COUNT + 2] = {0};
+    for (const ProfMark& m : g_marks) {
+        if (!m.b)
+            continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess)
+            acc[m.phase] += ms;
+    }
+    acc[PH_COUNT] = (double)g_launches;
+    if (g_last_ctr) {
+        u32 c[2] = {0, 0};
+        if (cudaMemcpy(c, g_last_ctr->c, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess)
+            acc[PH_COUNT + 1] = c[1];
+    }
+    int32_t k = 0;
+    for (; k < cap && k < PH_COUNT + 2; ++k)
+        out[k] = acc[k];
+    return k;
+}
+
+const char* appd_status_str(appd_status st)
+{
+    switch (st) {
+    case APPD_OK: return "APPD_OK";
+    case APPD_ERR_INVALID: return "APPD_ERR_INVALID";
+    case APPD_ERR_TOO_LARGE: return "APPD_ERR_TOO_LARGE";
+    case APPD_ERR_NOMEM: return "APPD_ERR_NOMEM";
+    case APPD_ERR_CUDA: return "APPD_ERR_CUDA";
+    case APPD_ERR_ASYMMETRIC: return "APPD_ERR_ASYMMETRIC";
+    case APPD_ERR_TIMEOUT: return "APPD_ERR_TIMEOUT";
+    case APPD_ERR_BUSY: return "APPD_ERR_BUSY";
+    case APPD_ERR_ALIAS: return "APPD_ERR_ALIAS";
+    case APPD_ERR_NOT_FOUND: return "APPD_ERR_NOT_FOUND";
+    case APPD_ERR_INTERNAL: return "APPD_ERR_INTERNAL";
+    }
+    return "APPD_ERR_UNKNOWN";
+}
+
+appd_status appd_solve(const void* W, int64_t n, appd_dtype dt, void* M, appd_stream_t s)
+{
+    return solve_impl(W, n, (int)dt, M, (cudaStream_t)s, false);
+}
+
+appd_status appd_solve_alg4(const void* W, int64_t n, appd_dtype dt, void* M, appd_stream_t s)
+{
+    return solve_impl(W, n, (int)dt, M, (cudaStream_t)s, true);
+}
+
+appd_status appd_solve_host(const void* W_host, int64_t n, appd_dtype dt, void* M_host,
+                            appd_stream_t s)
+{
+    appd_status st = check_args(W_host, n, (int)dt, M_host);
+    if (st != APPD_OK || n == 0)
+        return st;
+    cudaStream_t cs = (cudaStream_t)s;
+    const size_t bytes = (size_t)n * (size_t)n * 4;
+    void *dW = nullptr, *dM = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        Workspace* w = nullptr;
+        if ((st = get_ws(n, &w)) != APPD_OK)
+            return st;
+        if (w->host_bytes < bytes) {
+            cudaStreamSynchronize(cs);
+            cudaFree(w->hostW);
+            cudaFree(w->hostM);
+            w->hostW = w->hostM = nullptr;
+            w->host_bytes = 0;
+            cudaError_t e = cudaMalloc(&w->hostW, bytes);
+            if (e != cudaSuccess)
+                return cuda_fail(e);
+            e = cudaMalloc(&w->hostM, bytes);
+            if (e != cudaSuccess) {
+                cudaFree(w->hostW);
+                w->hostW = nullptr;
+                return cuda_fail(e);
+            }
+            w->host_bytes = bytes;
+        }
+        dW = w->hostW;
+        dM = w->hostM;
+    }
+    cudaError_t e = cudaMemcpyAsync(dW, W_host, bytes, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    st = solve_impl(dW, n, (int)dt, dM, cs, false);
+    if (st != APPD_OK)
+        return st;
+    e = cudaMemcpyAsync(M_host, dM, bytes, cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    e = cudaStreamSynchronize(cs);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
+appd_status appd_mst(const void* W, int64_t n, appd_dtype dt, uint64_t* edges_out, appd_stream_t s)
+{
+    appd_status st = check_args(W, n, (int)dt, edges_out);
+    if (st == APPD_ERR_ALIAS)
+        st = APPD_OK;
+    if (st != APPD_OK || n <= 1)
+        return st;
+    std::lock_guard<std::mutex> lk(g_mu);
+    SolveCtx c;
+    if ((st = prepare(n, c)) != APPD_OK)
+        return st;
+    if ((st = ensure_cscratch(*c.ws, n)) != APPD_OK)
+        return st;
+    if ((st = mst_and_order(c, W, n, (int)dt, c.ws->cscratch, false, (cudaStream_t)s)) != APPD_OK)
+        return st;
+    cudaError_t e = cudaMemcpyAsync(edges_out, c.ws->mst, (size_t)(n - 1) * 8,
+                                    cudaMemcpyDeviceToDevice, (cudaStream_t)s);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
+appd_status appd_leaf_order(const void* W, int64_t n, appd_dtype dt, uint32_t* pos_out,
+                            uint32_t* gap_out, appd_stream_t s)
+{
+    if (n < 0 || !W || !pos_out || (n > 1 && !gap_out) || ((int)dt != APPD_F32 && (int)dt != APPD_U32))
+        return APPD_ERR_INVALID;
+    if (n > 65536)
+        return APPD_ERR_TOO_LARGE;
+    if (n == 0)
+        return APPD_OK;
+    cudaStream_t cs = (cudaStream_t)s;
+    if (n == 1) {
+        cudaError_t e = cudaMemsetAsync(pos_out, 0, 4, cs);
+        return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    SolveCtx c;
+    appd_status st;
+    if ((st = prepare(n, c)) != APPD_OK)
+        return st;
+    if ((st = ensure_cscratch(*c.ws, n)) != APPD_OK)
+        return st;
+    if ((st = mst_and_order(c, W, n, (int)dt, c.ws->cscratch, true, cs)) != APPD_OK)
+        return st;
+    cudaError_t e = cudaMemcpyAsync(pos_out, c.ws->pos, (size_t)n * 4, cudaMemcpyDeviceToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(gap_out, c.ws->gap, (size_t)(n - 1) * 4, cudaMemcpyDeviceToDevice, cs);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
+appd_status appd_solve_batched(const int64_t* offsets, const void* Ws, const int64_t* ns,
+                               const uint8_t* dts, void* Ms, int32_t count, appd_stream_t s)
+{
+    if (count < 0 || (count > 0 && (!offsets || !ns || !Ws || !Ms)))
+        return APPD_ERR_INVALID;
+    for (int32_t g = 0; g < count; ++g) {
+        if (ns[g] < 0 || offsets[g] < 0)
+            return APPD_ERR_INVALID;
+        if (ns[g] > 65536)
+            return APPD_ERR_TOO_LARGE;
+        if (dts && dts[g] != APPD_F32 && dts[g] != APPD_U32)
+            return APPD_ERR_INVALID;
+    }
+    for (int32_t g = 0; g < count; ++g) {
+        const u32* W = (const u32*)Ws + offsets[g];
+        u32* M = (u32*)Ms + offsets[g];
+        appd_status st = appd_solve(W, ns[g], dts ? (appd_dtype)dts[g] : APPD_F32, M, s);
+        if (st != APPD_OK)
+            return st;
+    }
+    return APPD_OK;
+}
+
+appd_status appd_check_symmetric(const void* W, int64_t n, appd_dtype dt, appd_stream_t s)
+{
+    if (n < 0 || !W || ((int)dt != APPD_F32 && (int)dt != APPD_U32))
+        return APPD_ERR_INVALID;
+    if (n > 65536)
+        return APPD_ERR_TOO_LARGE;
+    if (n <= 1)
+        return APPD_OK;
+    u32* status = nullptr;
+    appd_status st;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if ((st = get_status(&status)) != APPD_OK)
+            return st;
+    }
+    cudaStream_t cs = (cudaStream_t)s;
+    u32* flag = status + 16;   // scratch word next to the status word
+    cudaError_t e = cudaMemsetAsync(flag, 0, 4, cs);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    k_check_sym<<<1024, 256, 0, cs>>>((const u32*)W, (u32)n, flag);
+    u32 h = 0;
+    e = cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    return h ? APPD_ERR_ASYMMETRIC : APPD_OK;
+}
+
+appd_status appd_last_device_status(appd_stream_t s)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)s);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    u32* status = nullptr;
+    appd_status st;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if ((st = get_status(&status)) != APPD_OK)
+            return st;
+    }
+    u32 h = 0;
+    e = cudaMemcpy(&h, status, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    if (h) {
+        e = cudaMemset(status, 0, 4);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+    }
+    if (h & DEV_TIMEOUT)
+        return APPD_ERR_TIMEOUT;
+    if (h & DEV_INTERNAL)
+        return APPD_ERR_INTERNAL;
+    return APPD_OK;
+}
+
+appd_status appd_release_workspaces(void)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return APPD_ERR_CUDA;
+    cudaDeviceSynchronize();
+    if (g_ws[dev]) {
+        cudaFree(g_ws[dev]->base);
+        cudaFree(g_ws[dev]->cscratch);
+        cudaFree(g_ws[dev]->hostW);
+        cudaFree(g_ws[dev]->hostM);
+        delete g_ws[dev];
+        g_ws[dev] = nullptr;
+    }
+    return APPD_OK;
+}
+
+}  // extern "C"

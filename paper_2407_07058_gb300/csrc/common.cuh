@@ -1,0 +1,272 @@
+// common.cuh -- device helpers shared by the APPD kernels (sm_103a).
+//
+// Order keys: a 32-bit key whose unsigned order is the weight order.  For
+// uint32 weights the key is the value; for FP32 it is IEEE-754 totalOrder
+// (non-negative: bits | 0x80000000, negative: ~bits).  The transform is a
+// bijection, so outputs are recovered bit-exactly from keys.
+//
+// Packed edges: key << 32 | lo << 16 | hi (lo < hi, both < 65536).  Unsigned
+// comparison of packed edges is a strict total order that refines the weight
+// order, which makes the MST unique and Boruvka's hooking cycle-free.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace appd {
+
+using u64 = unsigned long long;
+using u32 = unsigned int;
+
+constexpr u64 EDGE_INF = ~0ull;
+constexpr u32 NONE32 = 0xFFFFFFFFu;
+
+// device status bits (per device, read by appd_last_device_status)
+constexpr u32 DEV_TIMEOUT = 1u;
+constexpr u32 DEV_INTERNAL = 2u;
+
+// A bounded grid barrier gives up after this long (ns) and reports a timeout.
+constexpr u64 BARRIER_TIMEOUT_NS = 2000000000ull;
+
+__host__ __device__ __forceinline__ u32 key_of(u32 bits, int dt)
+{
+    u32 m = (u32)((int)bits >> 31) | 0x80000000u;
+    return dt ? bits : (bits ^ m);
+}
+
+__host__ __device__ __forceinline__ u32 bits_of(u32 key, int dt)
+{
+    return dt ? key : (key ^ ((key >> 31) ? 0x80000000u : 0xFFFFFFFFu));
+}
+
+__host__ __device__ __forceinline__ u64 pack_edge(u32 key, u32 a, u32 b)
+{
+    u32 lo = a < b ? a : b, hi = a < b ? b : a;
+    return ((u64)key << 32) | ((u64)lo << 16) | (u64)hi;
+}
+
+__host__ __device__ __forceinline__ u32 edge_key(u64 e) { return (u32)(e >> 32); }
+__host__ __device__ __forceinline__ u32 edge_lo(u64 e) { return (u32)(e >> 16) & 0xFFFFu; }
+__host__ __device__ __forceinline__ u32 edge_hi(u64 e) { return (u32)e & 0xFFFFu; }
+
+__device__ __forceinline__ int ceil_log2_dev(u32 x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
+
+__device__ __forceinline__ u64 globaltimer_ns()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ u32 ld_acquire(const u32* p)
+{
+    u32 v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// streaming 16-byte load that does not allocate in L1
+__device__ __forceinline__ uint4 ld_stream_v4(const void* p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ u32 ld_stream_u32(const void* p)
+{
+    u32 v;
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ u64 warp_min_u64(u64 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        u64 w = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// min over the block; every thread gets the result.  sh: >= 32 u64 of smem.
+__device__ __forceinline__ u64 block_min_u64(u64 v, u64* sh)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_min_u64(v);
+    __syncthreads();
+    if (lane == 0)
+        sh[w] = v;
+    __syncthreads();
+    u64 r = EDGE_INF;
+    for (int i = 0; i < nw; ++i)
+        r = sh[i] < r ? sh[i] : r;
+    __syncthreads();
+    return r;
+}
+
+// exclusive scan over the block of one u32 per thread; *total gets the sum.
+// sh: >= 33 u32 of smem.
+__device__ __forceinline__ u32 block_excl_scan(u32 v, u32* total, u32* sh)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    u32 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        u32 y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    __syncthreads();
+    if (lane == 31)
+        sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        u32 s = lane < nw ? sh[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            u32 y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+            if (lane >= o)
+                s += y;
+        }
+        if (lane < nw)
+            sh[lane] = s;
+    }
+    __syncthreads();
+    u32 pre = (w ? sh[w - 1] : 0u) + x - v;
+    if (total)
+        *total = sh[nw - 1];
+    __syncthreads();
+    return pre;
+}
+
+// ------------------------------------------------------------ grid barrier
+// Generation barrier for cooperative launches (all CTAs co-resident).  The
+// wait is bounded: after BARRIER_TIMEOUT_NS a CTA records DEV_TIMEOUT and
+// returns false; callers then leave the kernel.  The count word must be zero
+// when the kernel starts (the host clears it before each launch).
+struct GridBar {
+    u32 count;
+    u32 gen;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBar* bar, u32* status)
+{
+    __shared__ u32 s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_ok = 1;
+    if (threadIdx.x == 0) {
+        u32 ok = 1;
+        // once any CTA has given up, every later barrier fails at once
+        if (ld_acquire(status) & DEV_TIMEOUT) {
+            s_ok = 0;
+        }
+        u32 g = ld_acquire(&bar->gen);
+        __threadfence();
+        u32 arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            u64 t0 = globaltimer_ns();
+            while (s_ok && ld_acquire(&bar->gen) == g) {
+                __nanosleep(40);
+                if (globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = s_ok && ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// A "team" is the set of threads that cooperates on one phase: the whole
+// grid of a cooperative launch, or one CTA.  Phases are written once for both.
+struct GridTeam {
+    GridBar* bar;
+    u32* status;
+    __device__ __forceinline__ u32 rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ u32 size() const { return gridDim.x * blockDim.x; }
+    __device__ __forceinline__ u32 block() const { return blockIdx.x; }
+    __device__ __forceinline__ u32 nblocks() const { return gridDim.x; }
+    __device__ __forceinline__ bool sync() const { return grid_sync(bar, status); }
+};
+
+struct BlockTeam {
+    __device__ __forceinline__ u32 rank() const { return threadIdx.x; }
+    __device__ __forceinline__ u32 size() const { return blockDim.x; }
+    __device__ __forceinline__ u32 block() const { return 0; }
+    __device__ __forceinline__ u32 nblocks() const { return 1; }
+    __device__ __forceinline__ bool sync() const
+    {
+        __syncthreads();
+        return true;
+    }
+};
+
+// Exclusive scan of in[0..L) into out[0..L) by a team; returns the total to
+// every thread.  part: >= nblocks()+1 u32 of global scratch (grid team).
+// Costs two team syncs (the caller's next phase may read out[] directly).
+template <class Team>
+__device__ bool team_excl_scan(const Team& t, const u32* in, u32* out, u32 L, u32* part,
+                               u32* total_out)
+{
+    __shared__ u32 sh_scan[40];
+    const u32 nb = t.nblocks(), b = t.block(), bd = blockDim.x;
+    const u32 chunk = (L + nb - 1) / nb;
+    const u32 beg = min(L, b * chunk), end = min(L, beg + chunk);
+    // phase 1: per-block sums
+    u32 local = 0;
+    for (u32 i = beg + threadIdx.x; i < end; i += bd)
+        local += in[i];
+    u32 bsum = 0;
+    block_excl_scan(local, &bsum, sh_scan);
+    if (nb > 1) {
+        if (threadIdx.x == 0)
+            part[b] = bsum;
+        if (!t.sync())
+            return false;
+    }
+    // phase 2: offset of this block, then a blocked scan of the chunk
+    u32 off = 0, tot = 0;
+    if (nb > 1) {
+        for (u32 i = threadIdx.x; i < nb; i += bd) {
+            u32 v = part[i];
+            if (i < b)
+                off += v;
+            tot += v;
+        }
+        // reduce off and tot over the block
+        u32 o2 = 0, t2 = 0;
+        block_excl_scan(off, &o2, sh_scan);
+        block_excl_scan(tot, &t2, sh_scan);
+        off = o2;
+        tot = t2;
+    } else {
+        tot = bsum;
+    }
+    u32 carry = off;
+    for (u32 base = beg; base < end; base += bd) {
+        u32 i = base + threadIdx.x;
+        u32 v = i < end ? in[i] : 0u;
+        u32 s = 0;
+        u32 p = block_excl_scan(v, &s, sh_scan);
+        if (i < end)
+            out[i] = carry + p;
+        carry += s;
+    }
+    *total_out = tot;
+    return true;
+}
+
+}  // namespace appd

@@ -1,0 +1,95 @@
+// internal.h -- workspace layout and launch functions shared by the library's
+// translation units.  Not part of the public ABI (see include/appd.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace appd {
+
+constexpr int MAX_LEVELS = 20;     // Boruvka levels: ceil(log2 65536) = 16, plus slack
+constexpr int CONTRACT_ROWS = 8;   // rows of the current matrix per contraction work item
+
+// Device-resident control block of one solve.
+struct Counters {
+    u32 c[MAX_LEVELS + 2];   // components per level; c[0] = n
+    u32 done;                // set when one component is left
+    u32 mst_count;           // MST edges recorded so far
+    u32 item_next;           // contraction work-queue head
+    u32 total_chunks;        // contraction chunks at the current level
+    u32 nbr;                 // bin ranges at the current level
+    u32 jump_flag[3];        // pointer-jumping convergence flags (rotating)
+    u32 fill_next;           // work-queue head of the Algorithm 4 fill
+    u32 fill_total;
+    u32 pad[2];
+    GridBar bar;             // grid barrier of the cooperative kernels
+};
+
+// One workspace per (device, n); everything a solve needs besides W and M.
+struct Workspace {
+    int device = -1;
+    int64_t cap = 0;         // allocated capacity (vertices)
+    int64_t n = 0;           // vertices of the solve being enqueued
+    int levels = 0;          // ceil(log2 n), >= 1
+    int st_levels = 0;       // sparse-table levels over n-1 gaps
+    int sms = 0;
+    int coop_blocks = 0;     // CTAs of the cooperative kernels
+    int coop_threads = 0;
+    int contract_blocks = 0;
+    u32 bin_cap = 0;         // u64 bins per contraction CTA
+    void* base = nullptr;
+    size_t bytes = 0;
+
+    Counters* ctr = nullptr;
+    u32* part = nullptr;     // scan partials (coop_blocks + 1)
+    // Boruvka
+    u64* best[2] = {nullptr, nullptr};
+    u32 *comp = nullptr, *hook = nullptr, *par = nullptr, *flag = nullptr, *rootid = nullptr,
+        *label = nullptr, *cnt = nullptr, *fillc = nullptr, *gstart = nullptr, *members = nullptr,
+        *nchunk = nullptr, *chunk_start = nullptr, *item_group = nullptr;
+    u64* mst = nullptr;
+    // dendrogram / leaf order
+    u32 *deg = nullptr, *adj_off = nullptr, *afill = nullptr, *adj = nullptr, *aslot = nullptr;
+    u32 *lr_d[2] = {nullptr, nullptr}, *lr_nx[2] = {nullptr, nullptr};
+    u32 *parent = nullptr, *pe_key = nullptr;
+    u64* ord = nullptr;
+    u32* jump = nullptr;
+    u64* mxo = nullptr;
+    u32* nha = nullptr;
+    u64* skey[2] = {nullptr, nullptr};
+    u32* hist = nullptr;
+    u32 ntiles = 0;
+    u32 *first_child = nullptr, *next_sib = nullptr;
+    u32 *pos = nullptr, *order = nullptr, *nsize = nullptr, *gap = nullptr, *st = nullptr;
+    u32* a4_start = nullptr;   // Algorithm 4 fill: tile prefix per edge
+    // contraction matrices when M cannot serve as scratch (M == W)
+    void* cscratch = nullptr;
+    size_t cscratch_bytes = 0;
+    // staging for appd_solve_host
+    void* hostW = nullptr;
+    void* hostM = nullptr;
+    size_t host_bytes = 0;
+};
+
+// launch sequence pieces (all asynchronous on the stream)
+cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbuf_bytes,
+                    u32* status, cudaStream_t s);
+cudaError_t run_leaf_order(Workspace& ws, u32* status, cudaStream_t s);
+cudaError_t run_fill(Workspace& ws, int dt, void* M, cudaStream_t s);
+cudaError_t run_fill_alg4(Workspace& ws, int dt, void* M, u32* status, cudaStream_t s);
+cudaError_t run_fill_trivial(int64_t n, void* M, cudaStream_t s);   // n == 1
+
+// profiling (appd_profile_begin/end): phases of a solve
+enum Phase { PH_ROWMIN = 0, PH_STEP, PH_CONTRACT0, PH_CONTRACT, PH_LEAF, PH_FILL, PH_COUNT };
+void prof_begin(int phase, cudaStream_t s);
+void prof_end(int phase, cudaStream_t s);
+void prof_launches(int k);
+
+// sizes
+size_t contraction_scratch_bytes(int64_t n);
+int ceil_log2(int64_t x);
+
+}  // namespace appd

@@ -1,0 +1,574 @@
+// mst_kernels.cu -- dense Boruvka minimum spanning tree of the complete graph.
+//
+// The paper builds the MST with Prim's algorithm in O(n^2) (Section 3).  Prim
+// is n sequential steps; on the GPU we use Boruvka instead, which reaches the
+// same tree (the MST is unique under the packed-edge order):
+//   round 1  (k_rowmin)   best[i] = min over j != i of packed(i, j)
+//   each round (k_step)   hook every component to the other end of its best
+//                         edge, break mutual pairs, pointer-jump to roots,
+//                         relabel, record the new MST edges, group the rows
+//                         of the current matrix by new component
+//   contraction (k_contract_*)  C_{r+1}(A,B) = min over rows a in A and
+//                         columns b in B (b's component != A) of C_r(a,b);
+//                         C_0 is W itself.  The same pass gives the next
+//                         round's best[A] = min over B of C_{r+1}(A,B).
+// The round count is data dependent (<= ceil(log2 n)); the host enqueues the
+// maximum number of rounds and finished rounds exit at once, so a solve is a
+// fixed launch sequence with no host synchronisation.
+#include <cooperative_groups.h>
+
+#include "internal.h"
+
+namespace appd {
+
+int ceil_log2(int64_t x)
+{
+    int l = 0;
+    while ((int64_t(1) << l) < x)
+        ++l;
+    return l;
+}
+
+// ------------------------------------------------------------ round 1 (K1)
+// One CTA per row (grid-stride).  The tie-break inside one row is "smaller
+// column wins", which equals the packed order for a fixed row.
+template <int DT, bool VEC>
+__global__ void __launch_bounds__(256) k_rowmin(const u32* __restrict__ W, u32 n,
+                                                u64* __restrict__ best)
+{
+    __shared__ u64 sh[32];
+    for (u32 row = blockIdx.x; row < n; row += gridDim.x) {
+        const u32* r = W + (size_t)row * n;
+        u64 m = EDGE_INF;
+        auto take = [&](u32 bits, u32 j) {
+            u64 c = ((u64)key_of(bits, DT) << 32) | j;
+            if (j != row && c < m)
+                m = c;
+        };
+        if (VEC) {
+            const u32 n4 = n >> 2;
+            u32 g = threadIdx.x;
+            for (; g + 3 * 256 < n4; g += 4 * 256) {
+                uint4 v0 = ld_stream_v4(r + 4 * g);
+                uint4 v1 = ld_stream_v4(r + 4 * (g + 256));
+                uint4 v2 = ld_stream_v4(r + 4 * (g + 512));
+                uint4 v3 = ld_stream_v4(r + 4 * (g + 768));
+                take(v0.x, 4 * g), take(v0.y, 4 * g + 1), take(v0.z, 4 * g + 2), take(v0.w, 4 * g + 3);
+                u32 b1 = 4 * (g + 256);
+                take(v1.x, b1), take(v1.y, b1 + 1), take(v1.z, b1 + 2), take(v1.w, b1 + 3);
+                u32 b2 = 4 * (g + 512);
+                take(v2.x, b2), take(v2.y, b2 + 1), take(v2.z, b2 + 2), take(v2.w, b2 + 3);
+                u32 b3 = 4 * (g + 768);
+                take(v3.x, b3), take(v3.y, b3 + 1), take(v3.z, b3 + 2), take(v3.w, b3 + 3);
+            }
+            for (; g < n4; g += 256) {
+                uint4 v = ld_stream_v4(r + 4 * g);
+                take(v.x, 4 * g), take(v.y, 4 * g + 1), take(v.z, 4 * g + 2), take(v.w, 4 * g + 3);
+            }
+            for (u32 j = 4 * n4 + threadIdx.x; j < n; j += 256)
+                take(r[j], j);
+        } else {
+            for (u32 j = threadIdx.x; j < n; j += 256)
+                take(ld_stream_u32(r + j), j);
+        }
+        m = block_min_u64(m, sh);
+        if (threadIdx.x == 0)
+            best[row] = pack_edge((u32)(m >> 32), row, (u32)m & 0xFFFFu);
+    }
+}
+
+// --------------------------------------------------- Boruvka step (K2)
+struct StepArgs {
+    int level;
+    u32 n;
+    const u64* best_in;
+    u64* best_out;
+    u32 *comp, *hook, *par, *flag, *rootid, *label, *cnt, *fillc, *gstart, *members, *nchunk,
+        *chunk_start, *item_group;
+    u64* mst;
+    u64* cnext;
+    u32* part;
+    Counters* ctr;
+    u32* status;
+    u32 bin_cap;
+};
+
+__global__ void k_step(StepArgs a)
+{
+    GridTeam t{&a.ctr->bar, a.status};
+    Counters* ctr = a.ctr;
+    if (*(volatile u32*)&ctr->done)
+        return;
+    const int r = a.level;
+    const u32 c = ((volatile u32*)ctr->c)[r];
+    const u32 me = t.rank(), ts = t.size();
+    const u32 mst_base = *(volatile u32*)&ctr->mst_count;
+
+    // hook: the other end of each component's best edge
+    for (u32 x = me; x < c; x += ts) {
+        u64 e = a.best_in[x];
+        u32 h = x;
+        if (e != EDGE_INF && edge_lo(e) < a.n && edge_hi(e) < a.n) {
+            u32 ca = a.comp[edge_lo(e)], cb = a.comp[edge_hi(e)];
+            if (ca != x && cb != x)
+                atomicOr(a.status, DEV_INTERNAL);
+            h = (ca == x) ? cb : ca;
+        } else {
+            atomicOr(a.status, DEV_INTERNAL);
+        }
+        a.hook[x] = h < c ? h : x;
+        a.cnt[x] = 0;
+        a.fillc[x] = 0;
+    }
+    if (!t.sync())
+        return;
+    // mutual pairs share their best edge; the smaller id becomes the root
+    for (u32 x = me; x < c; x += ts) {
+        u32 b = a.hook[x];
+        bool root = (b < c && a.hook[b] == x && x < b);
+        a.par[x] = root ? x : (b < c ? b : x);
+    }
+    if (!t.sync())
+        return;
+    // pointer jumping to the roots; three rotating flags so that resetting
+    // the next round's flag never races with a late reader of this one
+    for (int it = 0; it < 64; ++it) {
+        volatile u32* fl = (volatile u32*)ctr->jump_flag;
+        if (me == 0)
+            fl[(it + 1) % 3] = 0;
+        bool changed = false;
+        for (u32 x = me; x < c; x += ts) {
+            u32 p = a.par[x], pp = a.par[p];
+            if (p != pp) {
+                a.par[x] = pp;
+                changed = true;
+            }
+        }
+        if (changed)
+            fl[it % 3] = 1;
+        if (!t.sync())
+            return;
+        if (fl[it % 3] == 0)
+            break;
+        if (it == 63 && me == 0)
+            atomicOr(a.status, DEV_INTERNAL);
+    }
+    for (u32 x = me; x < c; x += ts)
+        a.flag[x] = (a.par[x] == x) ? 1u : 0u;
+    if (!t.sync())
+        return;
+    u32 cn = 0;
+    if (!team_excl_scan(t, a.flag, a.rootid, c, a.part, &cn))
+        return;
+    if (!t.sync())
+        return;
+    // relabel, record MST edges of hooked components, group sizes
+    for (u32 x = me; x < c; x += ts) {
+        u32 p = a.par[x];
+        u32 A = a.rootid[p];
+        a.label[x] = A;
+        if (p != x)
+            a.mst[mst_base + x - a.rootid[x]] = a.best_in[x];
+        atomicAdd(&a.cnt[A], 1u);
+    }
+    if (!t.sync())
+        return;
+    for (u32 v = me; v < a.n; v += ts)
+        a.comp[v] = a.label[a.comp[v]];
+    for (u32 A = me; A < cn; A += ts) {
+        a.nchunk[A] = (a.cnt[A] + CONTRACT_ROWS - 1) / CONTRACT_ROWS;
+        a.best_out[A] = EDGE_INF;
+    }
+    if (!t.sync())
+        return;
+    u32 csum = 0, total_chunks = 0;
+    if (!team_excl_scan(t, a.cnt, a.gstart, cn, a.part, &csum))
+        return;
+    if (!t.sync())
+        return;
+    if (!team_excl_scan(t, a.nchunk, a.chunk_start, cn, a.part, &total_chunks))
+        return;
+    if (!t.sync())
+        return;
+    // scatter component members; map chunks to groups; init multi-chunk rows
+    for (u32 x = me; x < c; x += ts) {
+        u32 A = a.label[x];
+        u32 s = atomicAdd(&a.fillc[A], 1u);
+        a.members[a.gstart[A] + s] = x;
+    }
+    for (u32 A = me; A < cn; A += ts) {
+        u32 s0 = a.chunk_start[A], k = a.nchunk[A];
+        for (u32 q = 0; q < k; ++q)
+            a.item_group[s0 + q] = A;
+    }
+    if (cn > 1) {
+        for (u32 A = t.block(); A < cn; A += t.nblocks()) {
+            if (a.nchunk[A] > 1) {
+                u64* row = a.cnext + (size_t)A * cn;
+                for (u32 b = threadIdx.x; b < cn; b += blockDim.x)
+                    row[b] = EDGE_INF;
+            }
+        }
+    }
+    if (me == 0) {
+        a.gstart[cn] = c;
+        a.chunk_start[cn] = total_chunks;
+        ctr->c[r + 1] = cn;
+        ctr->total_chunks = total_chunks;
+        ctr->nbr = (cn + a.bin_cap - 1) / a.bin_cap;
+        ctr->item_next = 0;
+        ctr->mst_count = mst_base + (c - cn);
+        if (cn <= 1)
+            ctr->done = 1;
+    }
+}
+
+// ------------------------------------------------------ contraction (K3)
+struct ContractArgs {
+    int level;
+    const void* cin;     // W (level 0) or C_r
+    u64* cout;           // C_{r+1}
+    u64* best_out;
+    const u32 *label, *members, *gstart, *nchunk, *chunk_start, *item_group;
+    Counters* ctr;
+    u32 bin_cap;
+};
+
+// Loads the rows of one work item and reduces each column over them.
+// Level 0 reads W (4-byte weights) and builds packed edges; later levels
+// read packed u64 entries of C_r.
+template <int DT, int LEVEL0, bool VEC>
+__global__ void __launch_bounds__(1024, 1) k_contract(ContractArgs a)
+{
+    extern __shared__ __align__(16) u64 bins[];
+    __shared__ u32 s_item, s_rows[CONTRACT_ROWS];
+    __shared__ u64 s_red[32];
+    Counters* ctr = a.ctr;
+    if (*(volatile u32*)&ctr->done)
+        return;
+    const int r = a.level;
+    const u32 cr = ((volatile u32*)ctr->c)[r];       // columns of C_r (and rows)
+    const u32 cn = ((volatile u32*)ctr->c)[r + 1];   // size of C_{r+1}
+    const u32 total_chunks = *(volatile u32*)&ctr->total_chunks;
+    const u32 nbr = *(volatile u32*)&ctr->nbr;
+    const u32 total = total_chunks * nbr;
+    const u32 tid = threadIdx.x, bd = blockDim.x;
+
+    for (;;) {
+        if (tid == 0)
+            s_item = atomicAdd(&ctr->item_next, 1u);
+        __syncthreads();
+        const u32 item = s_item;
+        if (item >= total)
+            break;
+        const u32 br = item / total_chunks, ch = item - br * total_chunks;
+        const u32 A = a.item_group[ch];
+        const u32 k = ch - a.chunk_start[A];
+        const u32 m0 = a.gstart[A] + k * CONTRACT_ROWS;
+        const u32 m1 = min(a.gstart[A + 1], m0 + CONTRACT_ROWS);
+        const u32 nrows = m1 - m0;
+        const bool single = a.nchunk[A] == 1;
+        const u32 b0 = br * a.bin_cap;
+        const u32 nb = min(cn - b0, a.bin_cap);
+        if (tid < nrows)
+            s_rows[tid] = a.members[m0 + tid];
+        for (u32 b = tid; b < nb; b += bd)
+            bins[b] = EDGE_INF;
+        __syncthreads();
+        if (LEVEL0 && tid == 0) {
+            // ascending row order makes "first strictly smaller" = packed order
+            for (u32 i = 1; i < nrows; ++i) {
+                u32 v = s_rows[i], j = i;
+                while (j > 0 && s_rows[j - 1] > v) {
+                    s_rows[j] = s_rows[j - 1];
+                    --j;
+                }
+                s_rows[j] = v;
+            }
+        }
+        __syncthreads();
+        u32 rows[CONTRACT_ROWS];
+#pragma unroll
+        for (int q = 0; q < CONTRACT_ROWS; ++q)
+            rows[q] = (q < (int)nrows) ? s_rows[q] : s_rows[0];
+
+        auto update = [&](u32 L, u64 e) {
+            u32 rel = L - b0;
+            if (L != A && rel < nb) {
+                u64* slot = &bins[rel];
+                if (e < *slot)
+                    atomicMin(slot, e);
+            }
+        };
+
+        if (LEVEL0) {
+            const u32* Wp = (const u32*)a.cin;
+            auto column = [&](const u32* v, u32 j, u32 L) {
+                if (L == A || (L - b0) >= nb)
+                    return;
+                u32 bk = key_of(v[0], DT), bi = 0;
+#pragma unroll
+                for (int q = 1; q < CONTRACT_ROWS; ++q) {
+                    if (q < (int)nrows) {
+                        u32 kk = key_of(v[q], DT);
+                        if (kk < bk) {
+                            bk = kk;
+                            bi = q;
+                        }
+                    }
+                }
+                update(L, pack_edge(bk, s_rows[bi], j));
+            };
+            if (VEC) {
+                const u32 n4 = cr >> 2;
+                for (u32 g = tid; g < n4; g += bd) {
+                    uint4 v[CONTRACT_ROWS];
+#pragma unroll
+                    for (int q = 0; q < CONTRACT_ROWS; ++q)
+                        if (q < (int)nrows)
+                            v[q] = ld_stream_v4(Wp + (size_t)rows[q] * cr + 4 * g);
+                    uint4 lab = *(const uint4*)(a.label + 4 * g);
+                    u32 col[CONTRACT_ROWS];
+#pragma unroll
+                    for (int q = 0; q < CONTRACT_ROWS; ++q)
+                        col[q] = v[q].x;
+                    column(col, 4 * g, lab.x);
+#pragma unroll
+                    for (int q = 0; q < CONTRACT_ROWS; ++q)
+                        col[q] = v[q].y;
+                    column(col, 4 * g + 1, lab.y);
+#pragma unroll
+                    for (int q = 0; q < CONTRACT_ROWS; ++q)
+                        col[q] = v[q].z;
+                    column(col, 4 * g + 2, lab.z);
+#pragma unroll
+                    for (int q = 0; q < CONTRACT_ROWS; ++q)
+                        col[q] = v[q].w;
+                    column(col, 4 * g + 3, lab.w);
+                }
+                for (u32 j = 4 * n4 + tid; j < cr; j += bd) {
+                    u32 col[CONTRACT_ROWS];
+#pragma unroll
+                    for (int q = 0; q < CONTRACT_ROWS; ++q)
+                        col[q] = (q < (int)nrows) ? Wp[(size_t)rows[q] * cr + j] : 0u;
+                    column(col, j, a.label[j]);
+                }
+            } else {
+                for (u32 j = tid; j < cr; j += bd) {
+                    u32 col[CONTRACT_ROWS];
+#pragma unroll
+                    for (int q = 0; q < CONTRACT_ROWS; ++q)
+                        col[q] = (q < (int)nrows) ? ld_stream_u32(Wp + (size_t)rows[q] * cr + j) : 0u;
+                    column(col, j, a.label[j]);
+                }
+            }
+        } else {
+            const u64* Cp = (const u64*)a.cin;
+            const bool vec2 = ((cr & 1u) == 0) && (((uintptr_t)Cp & 15u) == 0);
+            u32 jstart = 0;
+            if (vec2) {
+                const u32 n2 = cr >> 1;
+                for (u32 g = tid; g < n2; g += bd) {
+                    uint4 v[CONTRACT_ROWS];
+#pragma unroll
+                    for (int q = 0; q < CONTRACT_ROWS; ++q)
+                        if (q < (int)nrows)
+                            v[q] = ld_stream_v4(Cp + (size_t)rows[q] * cr + 2 * g);
+                    uint2 lab = *(const uint2*)(a.label + 2 * g);
+                    u64 e0 = EDGE_INF, e1 = EDGE_INF;
+#pragma unroll
+                    for (int q = 0; q < CONTRACT_ROWS; ++q) {
+                        if (q < (int)nrows) {
+                            u64 x0 = ((u64)v[q].y << 32) | v[q].x;
+                            u64 x1 = ((u64)v[q].w << 32) | v[q].z;
+                            e0 = x0 < e0 ? x0 : e0;
+                            e1 = x1 < e1 ? x1 : e1;
+                        }
+                    }
+                    update(lab.x, e0);
+                    update(lab.y, e1);
+                }
+                jstart = 2 * n2;
+            }
+            for (u32 j = jstart + tid; j < cr; j += bd) {
+                u64 e = EDGE_INF;
+#pragma unroll
+                for (int q = 0; q < CONTRACT_ROWS; ++q) {
+                    if (q < (int)nrows) {
+                        u64 x = Cp[(size_t)rows[q] * cr + j];
+                        e = x < e ? x : e;
+                    }
+                }
+                update(a.label[j], e);
+            }
+        }
+        __syncthreads();
+        // write row A of C_{r+1} (this bin range) and fold the row minimum
+        u64 m = EDGE_INF;
+        u64* dst = a.cout + (size_t)A * cn + b0;
+        for (u32 b = tid; b < nb; b += bd) {
+            u64 v = bins[b];
+            if (single)
+                dst[b] = v;
+            else if (v != EDGE_INF)
+                atomicMin(dst + b, v);
+            m = v < m ? v : m;
+        }
+        m = block_min_u64(m, s_red);
+        if (tid == 0 && m != EDGE_INF)
+            atomicMin(&a.best_out[A], m);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ host
+namespace {
+
+__global__ void k_mst_init(Counters* ctr, u32* comp, u32 n, u32 bar_reset)
+{
+    for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        comp[v] = v;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int i = 0; i < MAX_LEVELS + 2; ++i)
+            ctr->c[i] = 0;
+        ctr->c[0] = n;
+        ctr->done = (n <= 1) ? 1u : 0u;
+        ctr->mst_count = 0;
+        ctr->item_next = 0;
+        ctr->total_chunks = 0;
+        ctr->nbr = 0;
+        ctr->jump_flag[0] = ctr->jump_flag[1] = ctr->jump_flag[2] = 0;
+        if (bar_reset) {
+            ctr->bar.count = 0;
+        }
+    }
+}
+
+template <class K>
+cudaError_t set_smem(K kern, size_t bytes)
+{
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t contraction_scratch_bytes(int64_t n)
+{
+    size_t h = (size_t)(n / 2), q = (size_t)(n / 4);
+    return (h * h + q * q) * sizeof(u64) + 64;
+}
+
+cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbuf_bytes,
+                    u32* status, cudaStream_t s)
+{
+    const u32 n = (u32)ws.n;
+    cudaError_t err;
+    k_mst_init<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(ws.ctr, ws.comp, n, 1);
+    prof_launches(1);
+    if ((err = cudaGetLastError()) != cudaSuccess)
+        return err;
+    if (n <= 1)
+        return cudaSuccess;
+    const bool vec = (n % 4 == 0) && ((uintptr_t)W % 16 == 0);
+    prof_launches(1);
+    prof_begin(PH_ROWMIN, s);
+    {
+        int grid = ws.sms * 8;
+        if (grid > (int)n)
+            grid = (int)n;
+        if (dt == 0) {
+            if (vec)
+                k_rowmin<0, true><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+            else
+                k_rowmin<0, false><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+        } else {
+            if (vec)
+                k_rowmin<1, true><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+            else
+                k_rowmin<1, false><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+        }
+        if ((err = cudaGetLastError()) != cudaSuccess)
+            return err;
+    }
+    prof_end(PH_ROWMIN, s);
+    // contraction matrices: C_1, C_3, ... in the first half, C_2, C_4, ... after it
+    const size_t h = (size_t)(n / 2);
+    // the u64 matrices need 16-byte alignment; a caller's M may start anywhere
+    // 4-byte aligned (batched layouts), so round up (the buffer has slack)
+    u64* cb[2];
+    cb[0] = (u64*)(((uintptr_t)cbuf + 15) & ~(uintptr_t)15);
+    cb[1] = (u64*)((char*)cb[0] + ((h * h * sizeof(u64) + 15) & ~(size_t)15));
+    (void)cbuf_bytes;
+    const size_t smem = (size_t)ws.bin_cap * sizeof(u64);
+    auto k0 = (dt == 0) ? (vec ? k_contract<0, 1, true> : k_contract<0, 1, false>)
+                        : (vec ? k_contract<1, 1, true> : k_contract<1, 1, false>);
+    auto k1 = k_contract<0, 0, false>;
+    if ((err = set_smem(k0, smem)) != cudaSuccess)
+        return err;
+    if ((err = set_smem(k1, smem)) != cudaSuccess)
+        return err;
+    for (int r = 0; r < ws.levels; ++r) {
+        StepArgs sa;
+        sa.level = r;
+        sa.n = n;
+        sa.best_in = ws.best[r & 1];
+        sa.best_out = ws.best[(r + 1) & 1];
+        sa.comp = ws.comp;
+        sa.hook = ws.hook;
+        sa.par = ws.par;
+        sa.flag = ws.flag;
+        sa.rootid = ws.rootid;
+        sa.label = ws.label;
+        sa.cnt = ws.cnt;
+        sa.fillc = ws.fillc;
+        sa.gstart = ws.gstart;
+        sa.members = ws.members;
+        sa.nchunk = ws.nchunk;
+        sa.chunk_start = ws.chunk_start;
+        sa.item_group = ws.item_group;
+        sa.mst = ws.mst;
+        sa.cnext = cb[r & 1];
+        sa.part = ws.part;
+        sa.ctr = ws.ctr;
+        sa.status = status;
+        sa.bin_cap = ws.bin_cap;
+        err = cudaMemsetAsync(&ws.ctr->bar.count, 0, sizeof(u32), s);
+        if (err != cudaSuccess)
+            return err;
+        void* args[] = {&sa};
+        prof_begin(PH_STEP, s);
+        err = cudaLaunchCooperativeKernel((const void*)k_step, dim3(ws.coop_blocks),
+                                          dim3(ws.coop_threads), args, 0, s);
+        prof_end(PH_STEP, s);
+        prof_launches(2);
+        if (err != cudaSuccess)
+            return err;
+
+        ContractArgs ca;
+        ca.level = r;
+        ca.cin = (r == 0) ? W : (const void*)cb[(r - 1) & 1];
+        ca.cout = cb[r & 1];
+        ca.best_out = ws.best[(r + 1) & 1];
+        ca.label = ws.label;
+        ca.members = ws.members;
+        ca.gstart = ws.gstart;
+        ca.nchunk = ws.nchunk;
+        ca.chunk_start = ws.chunk_start;
+        ca.item_group = ws.item_group;
+        ca.ctr = ws.ctr;
+        ca.bin_cap = ws.bin_cap;
+        dim3 grid(ws.contract_blocks), block(1024);
+        const int ph = (r == 0) ? PH_CONTRACT0 : PH_CONTRACT;
+        prof_begin(ph, s);
+        if (r == 0)
+            k0<<<grid, block, smem, s>>>(ca);
+        else
+            k1<<<grid, block, smem, s>>>(ca);
+        prof_end(ph, s);
+        if ((err = cudaGetLastError()) != cudaSuccess)
+            return err;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace appd

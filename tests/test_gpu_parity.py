@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA path against the CPU oracle, bit for bit.
+
+Every output of the method is a selected input weight, so the bar is exact
+equality of the 32-bit patterns (no tolerance), for FP32 and uint32 weights,
+ties or not.  Inputs are seeded synthetic graphs from ``synth``.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2407_07058_gb300 import appd
+from tests.test_oracle_pins import keys_np, sym_random
+
+pytestmark = pytest.mark.gpu
+
+
+def to_dev(W: np.ndarray) -> torch.Tensor:
+    if W.dtype == np.float32:
+        return torch.from_numpy(W).cuda()
+    return torch.from_numpy(W.view(np.int32)).cuda()
+
+
+def from_dev(T: torch.Tensor, like: np.ndarray) -> np.ndarray:
+    return T.cpu().numpy().view(like.dtype)
+
+
+def assert_bits(got: np.ndarray, ref: np.ndarray, what=""):
+    g, r = got.view(np.uint32), ref.view(np.uint32)
+    if not np.array_equal(g, r):
+        bad = np.argwhere(g != r)
+        i, j = bad[0]
+        raise AssertionError(f"{what}: {len(bad)} cells differ; first at ({i},{j}): "
+                             f"got {g[i, j]:#010x} want {r[i, j]:#010x}")
+
+
+def solve_np(W: np.ndarray, alg4=False) -> np.ndarray:
+    T = to_dev(W)
+    M = appd.solve(T, alg4=alg4)
+    torch.cuda.synchronize()
+    assert appd.last_device_status() == 0
+    return from_dev(M, W)
+
+
+def special_values(n, rng):
+    pool = np.array([0xFFC00000, 0xFF800000, 0xBF800000, 0x80000000, 0x00000000, 0x3F800000,
+                     0x7F800000, 0x7FC00000, 0x40000000, 0x00000001], dtype=np.uint32)
+    B = pool[rng.integers(0, len(pool), size=(n, n))]
+    B = np.triu(B, 1)
+    B = B + B.T
+    np.fill_diagonal(B, 0)
+    return np.ascontiguousarray(B.astype(np.uint32)).view(np.float32)
+
+
+SIZES = [1, 2, 3, 4, 5, 7, 8, 9, 31, 32, 33, 64, 127, 128, 255, 257, 1000, 1031]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("kind", ["f32", "u32", "ties", "special"])
+def test_small_parity(n, kind):
+    rng = np.random.default_rng(1000 + n)
+    if kind == "f32":
+        W = sym_random(n, rng, np.float32)
+    elif kind == "u32":
+        W = sym_random(n, rng, np.uint32)
+    elif kind == "ties":
+        W = sym_random(n, rng, np.uint32, "ties")
+    else:
+        W = special_values(n, rng)
+    ref = oracle.appd(W)
+    assert_bits(solve_np(W), ref, f"n={n} {kind}")
+
+
+@pytest.mark.parametrize("n", [2, 3, 33, 257, 1000])
+def test_alg4_form_parity(n):
+    rng = np.random.default_rng(7 + n)
+    for W in (sym_random(n, rng, np.float32), sym_random(n, rng, np.uint32, "ties")):
+        assert_bits(solve_np(W, alg4=True), oracle.appd(W), f"alg4 n={n}")
+
+
+@pytest.mark.parametrize("n", [2, 5, 100, 1000, 4099])
+def test_mst_edge_set_equals_prim(n):
+    # Under the strict order (key, lo, hi) the MST is unique: the Boruvka edge
+    # set must equal the oracle's Prim edge set exactly.
+    W = synth.hash_u32(n, seed=n) if n % 2 else synth.uniform01(n, seed=n)
+    _, ref = oracle.prim(W)
+    E = appd.mst(to_dev(W)).cpu().numpy().view(np.uint64)
+    assert np.array_equal(np.sort(E), np.sort(ref))
+
+
+@pytest.mark.parametrize("n", [2, 3, 50, 777])
+def test_leaf_order_range_max(n):
+    W = synth.euclid(synth.gmm_points(n, 2, 5, sigma=0.5, seed=n, mean_box=10.0))
+    pos, gap = appd.leaf_order(to_dev(W))
+    pos = pos.cpu().numpy().astype(np.int64)
+    gap = gap.cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert sorted(pos.tolist()) == list(range(n))
+    K = keys_np(oracle.appd(W))
+    rng = np.random.default_rng(n)
+    for _ in range(2000):
+        i, j = rng.integers(0, n, 2)
+        if i == j:
+            continue
+        a, b = sorted((pos[i], pos[j]))
+        assert gap[a:b].max() == K[i, j]
+
+
+def test_in_place():
+    W = synth.euclid(synth.uniform_points(600, 2, seed=5))
+    ref = oracle.appd(W)
+    T = to_dev(W)
+    appd.solve(T, out=T)
+    torch.cuda.synchronize()
+    assert_bits(from_dev(T, W), ref, "in place")
+
+
+def test_repeat_and_workspace_reuse():
+    # different n on one workspace, twice, results identical each time
+    Ws = [synth.hash_u32(n, seed=n) for n in (300, 4000, 17, 300)]
+    refs = [oracle.appd(W) for W in Ws]
+    for _ in range(2):
+        for W, ref in zip(Ws, refs):
+            assert_bits(solve_np(W), ref)
+
+
+def test_check_symmetric():
+    W = synth.hash_u32(129, seed=1)
+    T = to_dev(W)
+    assert appd.check_symmetric(T)
+    T[3, 100] += 1
+    assert not appd.check_symmetric(T)
+
+
+def test_host_entry_point():
+    W = synth.euclid(synth.gmm_points(700, 2, 5, sigma=0.5, seed=8, mean_box=10.0))
+    assert_bits(appd.solve_host(W), oracle.appd(W), "solve_host")
+
+
+def test_config1_gmm_n1000():
+    W = synth.euclid(synth.cfg1_points())
+    ref = oracle.appd(W)
+    assert_bits(solve_np(W), ref, "config 1")
+    assert_bits(solve_np(W, alg4=True), ref, "config 1 alg4")
+
+
+@pytest.mark.parametrize("which", ["2a", "2b"])
+def test_config2_n16384(which):
+    if which == "2a":
+        W = synth.euclid(synth.cfg2a_points())
+    else:
+        W = synth.hash_u32(16384, seed=synth.CFG2B_SEED)
+    ref = oracle.appd(W)
+    assert_bits(solve_np(W), ref, f"config {which}")
+
+
+def test_batched_matches_single():
+    sizes = [32, 33, 100, 257, 64, 1000]
+    Ws = [synth.uniform01(n, seed=synth.cfg4_seed(g)) for g, n in enumerate(sizes)]
+    offs = np.cumsum([0] + [n * n for n in sizes])[:-1]
+    flat = torch.from_numpy(np.concatenate([W.ravel() for W in Ws])).cuda()
+    M = appd.solve_batched(flat, offs, sizes)
+    torch.cuda.synchronize()
+    Mh = M.cpu().numpy()
+    for g, (W, n) in enumerate(zip(Ws, sizes)):
+        got = Mh[offs[g]: offs[g] + n * n].reshape(n, n)
+        assert_bits(got, oracle.appd(W), f"batched graph {g}")
+
+
+@pytest.mark.parametrize("n", [8, 64, 100, 1000])
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_unaligned_pointers(n, shift):
+    # W and M start 4, 8 or 12 bytes past a 16-byte boundary
+    W = synth.uniform01(n, seed=n + shift)
+    ref = oracle.appd(W)
+    bufW = torch.zeros(n * n + 8, dtype=torch.float32, device="cuda")
+    bufM = torch.zeros(n * n + 8, dtype=torch.float32, device="cuda")
+    Wv = bufW[shift: shift + n * n].view(n, n)
+    Mv = bufM[shift: shift + n * n].view(n, n)
+    Wv.copy_(torch.from_numpy(W))
+    appd.solve(Wv, out=Mv)
+    torch.cuda.synchronize()
+    assert appd.last_device_status() == 0
+    assert_bits(Mv.cpu().numpy(), ref, f"unaligned n={n} shift={shift}")
