@@ -6,12 +6,13 @@
 // tile of 256 columns and a range of rows:
 //   - the columns' positions are sorted once per CTA (bitonic in smem);
 //   - A[k] = largest gap between consecutive sorted column positions (one
-//     sparse-table query each), with a small sparse table over A in smem;
-//   - per chunk of 32 rows, every row r with position p splits the sorted
-//     columns at t (columns left / right of p); the values for the sorted
-//     columns are running maxima of A outward from t, written into smem;
-//   - rows are stored coalesced (16-byte streaming stores), each output
-//     element once.  The kernel is bound by HBM write bandwidth.
+//     sparse-table query each);
+//   - every row with position p splits the sorted columns at t; its values
+//     are running maxima of A outward from t, combined with the largest gap
+//     from p to the nearest column on each side.  The running maxima for all
+//     t form a (FC+1) x FC table built once per CTA;
+//   - each warp writes whole row segments with 16-byte streaming stores,
+//     each output element once.  The kernel is bound by HBM write bandwidth.
 // k_a4_fill (comparison): Algorithm 4's calculation-and-copy (Sections 3, 5,
 // and the per-edge parallel variant of Section 6.2): one work item per MST
 // edge e fills the cross block tree1 x tree2 and its transpose with w(e).
@@ -22,9 +23,8 @@
 
 namespace appd {
 
-constexpr int FC = 256;   // columns per CTA
-constexpr int FR = 32;    // rows per chunk
-constexpr int FA_LEVELS = 8;
+constexpr int FC = 128;   // columns per CTA
+constexpr int FT = 256;   // threads per CTA
 
 __device__ __forceinline__ u32 rmq_gap(const u32* __restrict__ st, u32 stride, u32 a, u32 b)
 {
@@ -37,145 +37,140 @@ __device__ __forceinline__ u32 rmq_gap(const u32* __restrict__ st, u32 stride, u
     return x > y ? x : y;
 }
 
+// dynamic shared memory layout of k_fill
+struct FillSmem {
+    u32 T[FC + 1][FC];   // T[t][col]: running max of A outward from split t
+    u64 sort[FC];
+    u32 q[FC];           // sorted column positions
+    u32 col[FC];         // sorted index -> column offset
+    u32 rank[FC];        // column offset -> sorted index
+    u32 A[FC];           // A[k] = max gap between q[k] and q[k+1]
+};
+
+size_t fill_smem_bytes(u32 rows_per_cta) { return sizeof(FillSmem) + (size_t)rows_per_cta * 12; }
+
+// For a row with leaf position p, let t = #{sorted columns with q < p}.  Its
+// value at the column with sorted index k is max(R_p, A[t..k-1]) for k >= t
+// and max(L_p, A[k..t-2]) for k < t, where R_p / L_p are the largest gaps
+// from p to the nearest column on each side.  The A-parts depend only on
+// (t, k): they form the table T, built once per CTA, so each output element
+// costs one shared load, one max and the key-to-bits transform.
 template <int DT>
-__global__ void __launch_bounds__(256) k_fill(const u32* __restrict__ pos, const u32* __restrict__ st,
-                                              u32 n, u32 rows_per_cta, u32* __restrict__ M)
+__global__ void __launch_bounds__(FT, 2) k_fill(const u32* __restrict__ pos, const u32* __restrict__ st,
+                                                u32 n, u32 rows_per_cta, u32* __restrict__ M)
 {
-    __shared__ u64 s_sort[FC];
-    __shared__ u32 s_q[FC];
-    __shared__ u32 s_rank[FC];
-    __shared__ u32 s_A[FA_LEVELS][FC];
-    __shared__ u32 s_V[FR][FC + 1];
-    __shared__ u32 s_p[FR], s_t[FR], s_L[FR], s_R[FR];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FillSmem& S = *reinterpret_cast<FillSmem*>(smem_raw);
+    u32* s_t = reinterpret_cast<u32*>(smem_raw + sizeof(FillSmem));
+    u32* s_L = s_t + rows_per_cta;
+    u32* s_R = s_L + rows_per_cta;
 
     const u32 tid = threadIdx.x;
     const u32 j0 = blockIdx.x * FC;
     const u32 nc = min((u32)FC, n - j0);
+    const u32 r0 = blockIdx.y * rows_per_cta;
+    const u32 nr = min(rows_per_cta, n - r0);
 
-    u32 q = (tid < nc) ? __ldg(pos + j0 + tid) : 0xFFFFFFFFu;
-    s_sort[tid] = ((u64)q << 32) | tid;
+    // 1. sort the tile's column positions (bitonic, FC elements)
+    if (tid < FC)
+        S.sort[tid] = ((u64)(tid < nc ? __ldg(pos + j0 + tid) : 0xFFFFFFFFu) << 32) | tid;
     __syncthreads();
     for (u32 k = 2; k <= FC; k <<= 1) {
         for (u32 j = k >> 1; j > 0; j >>= 1) {
-            u32 ixj = tid ^ j;
-            if (ixj > tid) {
-                bool up = (tid & k) == 0;
-                u64 x = s_sort[tid], y = s_sort[ixj];
-                if ((x > y) == up) {
-                    s_sort[tid] = y;
-                    s_sort[ixj] = x;
+            if (tid < FC) {
+                u32 ixj = tid ^ j;
+                if (ixj > tid) {
+                    bool up = (tid & k) == 0;
+                    u64 x = S.sort[tid], y = S.sort[ixj];
+                    if ((x > y) == up) {
+                        S.sort[tid] = y;
+                        S.sort[ixj] = x;
+                    }
                 }
             }
             __syncthreads();
         }
     }
-    {
-        u64 e = s_sort[tid];
-        s_q[tid] = (u32)(e >> 32);
+    if (tid < FC) {
+        u64 e = S.sort[tid];
+        S.q[tid] = (u32)(e >> 32);
+        S.col[tid] = (u32)e;
         if (tid < nc)
-            s_rank[(u32)e] = tid;
+            S.rank[(u32)e] = tid;
     }
     __syncthreads();
+    // 2. gaps between consecutive sorted columns; row split points and sides
     if (tid + 1 < nc)
-        s_A[0][tid] = rmq_gap(st, n, s_q[tid], s_q[tid + 1] - 1);
-    __syncthreads();
-    for (int l = 1; l < FA_LEVELS; ++l) {
-        u32 h = 1u << (l - 1);
-        if (tid + 2 * h <= nc - 1) {
-            u32 x = s_A[l - 1][tid], y = s_A[l - 1][tid + h];
-            s_A[l][tid] = x > y ? x : y;
+        S.A[tid] = rmq_gap(st, n, S.q[tid], S.q[tid + 1] - 1);
+    for (u32 r = tid; r < nr; r += FT) {
+        u32 p = __ldg(pos + r0 + r);
+        u32 lo = 0, hi = nc;
+        while (lo < hi) {
+            u32 mid = (lo + hi) >> 1;
+            if (S.q[mid] < p)
+                lo = mid + 1;
+            else
+                hi = mid;
         }
-        __syncthreads();
+        s_t[r] = lo;
+        s_L[r] = lo > 0 ? rmq_gap(st, n, S.q[lo - 1], p - 1) : 0u;
+        s_R[r] = (lo < nc && S.q[lo] != p) ? rmq_gap(st, n, p, S.q[lo] - 1) : 0u;
     }
-    auto rangeA = [&](u32 a, u32 b) -> u32 {   // max A[a..b], 0 if empty
-        if ((int)b < (int)a)
-            return 0u;
-        u32 l = 31 - __clz(b - a + 1);
-        u32 x = s_A[l][a], y = s_A[l][b - (1u << l) + 1];
-        return x > y ? x : y;
-    };
-
-    const u32 r_begin = blockIdx.y * rows_per_cta;
-    const u32 r_end = min(n, r_begin + rows_per_cta);
+    __syncthreads();
+    // 3. the table: row t holds the running maxima outward from split t
+    if (tid <= nc) {
+        const u32 t = tid;
+        u32 cur = 0;
+        for (u32 k = t; k < nc; ++k) {
+            if (k > t) {
+                u32 a = S.A[k - 1];
+                cur = cur > a ? cur : a;
+            }
+            S.T[t][S.col[k]] = cur;
+        }
+        cur = 0;
+        for (u32 k = t; k-- > 0;) {
+            if (k + 1 < t) {
+                u32 a = S.A[k];
+                cur = cur > a ? cur : a;
+            }
+            S.T[t][S.col[k]] = cur;
+        }
+    }
+    __syncthreads();
+    // 4. rows: one warp per row, each lane four consecutive columns
     const u32 lane = tid & 31, w = tid >> 5;
-    const bool vec = (n % 4u) == 0 && (((uintptr_t)M & 15u) == 0);
-    for (u32 i0 = r_begin; i0 < r_end; i0 += FR) {
-        const u32 nr = min((u32)FR, r_end - i0);
-        if (tid < nr) {
-            u32 p = __ldg(pos + i0 + tid);
-            u32 lo = 0, hi = nc;
-            while (lo < hi) {
-                u32 mid = (lo + hi) >> 1;
-                if (s_q[mid] < p)
-                    lo = mid + 1;
-                else
-                    hi = mid;
+    const bool vec = (nc == FC) && (n % 4u) == 0 && (((uintptr_t)M & 15u) == 0);
+    if (vec) {
+        const u32 jj = 4 * lane;
+        const uint4 rk = *reinterpret_cast<const uint4*>(&S.rank[jj]);
+        for (u32 r = w; r < nr; r += FT / 32) {
+            const u32 t = s_t[r], L = s_L[r], R = s_R[r];
+            const uint4 tv = *reinterpret_cast<const uint4*>(&S.T[t][jj]);
+            u32 v0 = max(tv.x, rk.x >= t ? R : L);
+            u32 v1 = max(tv.y, rk.y >= t ? R : L);
+            u32 v2 = max(tv.z, rk.z >= t ? R : L);
+            u32 v3 = max(tv.w, rk.w >= t ? R : L);
+            uint4 o = make_uint4(bits_of(v0, DT), bits_of(v1, DT), bits_of(v2, DT), bits_of(v3, DT));
+            const u32 i = r0 + r;
+            const u32 dc = i - j0 - jj;     // the diagonal cell is all-zero bits
+            if (dc < 4u) {
+                if (dc == 0) o.x = 0u;
+                if (dc == 1) o.y = 0u;
+                if (dc == 2) o.z = 0u;
+                if (dc == 3) o.w = 0u;
             }
-            u32 Lv = 0, Rv = 0;
-            if (lo > 0)
-                Lv = rmq_gap(st, n, s_q[lo - 1], p - 1);
-            if (lo < nc && s_q[lo] != p)
-                Rv = rmq_gap(st, n, p, s_q[lo] - 1);
-            s_p[tid] = p;
-            s_t[tid] = lo;
-            s_L[tid] = Lv;
-            s_R[tid] = Rv;
+            __stcs(reinterpret_cast<uint4*>(M + (size_t)i * n + j0 + jj), o);
         }
-        __syncthreads();
-        if (lane < nr) {
-            const u32 t = s_t[lane], p = s_p[lane];
-            const u32 ks = 32 * w, ke = min(ks + 32, nc);
-            // right of the row's position: running max upward from t
-            u32 k = max(ks, t);
-            if (k < ke) {
-                u32 cur = s_R[lane];
-                u32 pre = rangeA(t, k - 1);
-                cur = cur > pre ? cur : pre;
-                for (;;) {
-                    bool diag = (k == t) && (s_q[t] == p);
-                    s_V[lane][k] = diag ? 0u : bits_of(cur, DT);
-                    if (++k >= ke)
-                        break;
-                    u32 a = s_A[0][k - 1];
-                    cur = cur > a ? cur : a;
-                }
-            }
-            // left of it: running max downward from t-1
-            const u32 kt = min(ke, t);
-            if (kt > ks) {
-                k = kt - 1;
-                u32 cur = s_L[lane];
-                u32 pre = rangeA(k, t - 2);
-                cur = cur > pre ? cur : pre;
-                for (;;) {
-                    s_V[lane][k] = bits_of(cur, DT);
-                    if (k == ks)
-                        break;
-                    --k;
-                    u32 a = s_A[0][k];
-                    cur = cur > a ? cur : a;
-                }
+    } else {
+        for (u32 r = w; r < nr; r += FT / 32) {
+            const u32 t = s_t[r], L = s_L[r], R = s_R[r];
+            const u32 i = r0 + r;
+            for (u32 c = lane; c < nc; c += 32) {
+                u32 v = max(S.T[t][c], S.rank[c] >= t ? R : L);
+                M[(size_t)i * n + j0 + c] = (j0 + c == i) ? 0u : bits_of(v, DT);
             }
         }
-        __syncthreads();
-        if (vec) {
-            const u32 g4 = nc >> 2;
-            for (u32 g = tid; g < nr * g4; g += 256) {
-                const u32 rr = g / g4, c4 = g - rr * g4, jj = 4 * c4;
-                uint4 o;
-                o.x = s_V[rr][s_rank[jj]];
-                o.y = s_V[rr][s_rank[jj + 1]];
-                o.z = s_V[rr][s_rank[jj + 2]];
-                o.w = s_V[rr][s_rank[jj + 3]];
-                __stcs(reinterpret_cast<uint4*>(M + (size_t)(i0 + rr) * n + j0 + jj), o);
-            }
-        } else {
-            for (u32 g = tid; g < nr * nc; g += 256) {
-                const u32 rr = g / nc, jj = g - rr * nc;
-                M[(size_t)(i0 + rr) * n + j0 + jj] = s_V[rr][s_rank[jj]];
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -262,19 +257,27 @@ cudaError_t run_fill(Workspace& ws, int dt, void* M, cudaStream_t s)
     if (n == 1)
         return cudaMemsetAsync(M, 0, sizeof(u32), s);
     const u32 gx = (n + FC - 1) / FC;
-    // enough CTAs to fill the GPU, but at least 32 rows per CTA
-    u64 target = (u64)ws.sms * 8;
+    // rows per CTA: enough CTAs for several waves, at most 1024 rows
+    u64 target = (u64)ws.sms * 2 * 4;
     u32 rows = (u32)(((u64)n * gx + target - 1) / target);
-    rows = (rows + FR - 1) / FR * FR;
-    if (rows < FR)
-        rows = FR;
+    if (rows < 32)
+        rows = 32;
     if (rows > 1024)
         rows = 1024;
     dim3 grid(gx, (n + rows - 1) / rows);
-    if (dt == 0)
-        k_fill<0><<<grid, 256, 0, s>>>(ws.pos, ws.st, n, rows, (u32*)M);
-    else
-        k_fill<1><<<grid, 256, 0, s>>>(ws.pos, ws.st, n, rows, (u32*)M);
+    const size_t smem = fill_smem_bytes(rows);
+    cudaError_t e;
+    if (dt == 0) {
+        if ((e = cudaFuncSetAttribute(k_fill<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)fill_smem_bytes(1024))) != cudaSuccess)
+            return e;
+        k_fill<0><<<grid, FT, smem, s>>>(ws.pos, ws.st, n, rows, (u32*)M);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_fill<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)fill_smem_bytes(1024))) != cudaSuccess)
+            return e;
+        k_fill<1><<<grid, FT, smem, s>>>(ws.pos, ws.st, n, rows, (u32*)M);
+    }
     return cudaGetLastError();
 }
 

@@ -12,6 +12,7 @@ namespace appd {
 
 constexpr int MAX_LEVELS = 20;     // Boruvka levels: ceil(log2 65536) = 16, plus slack
 constexpr int CONTRACT_ROWS = 8;   // rows of the current matrix per contraction work item
+constexpr int CONTRACT_THREADS = 1024;
 
 // Device-resident control block of one solve.
 struct Counters {

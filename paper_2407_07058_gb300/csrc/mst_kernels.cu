@@ -77,6 +77,80 @@ __global__ void __launch_bounds__(256) k_rowmin(const u32* __restrict__ W, u32 n
     }
 }
 
+// Round 1 over the upper triangle only (K1, symmetric form).  W is
+// symmetric, so element (i, j), i < j, is both a candidate for row i and for
+// row j.  A CTA owns 128 rows x 1024 columns; each warp a 128-column slab.
+// Lanes own 4 columns: their column minima over the CTA's rows give row j's
+// candidates from rows i < j; per-row minima are warp reductions
+// (redux.sync) merged across warps in shared memory.  Both go to best[] with 64-bit atomic minima on packed edges, so
+// every unordered pair is read once (half of W).  best[] starts at +inf.
+constexpr u32 RS_ROWS = 128, RS_COLS = 1024;
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u32 n,
+                                                    u64* __restrict__ best)
+{
+    __shared__ u64 s_row[RS_ROWS];
+    const u32 i0 = blockIdx.y * RS_ROWS, c0 = blockIdx.x * RS_COLS;
+    if (c0 + RS_COLS - 1 <= i0 || i0 >= n || c0 >= n)   // no pair i < j in this tile
+        return;
+    const u32 w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (u32 r = threadIdx.x; r < RS_ROWS; r += blockDim.x)
+        s_row[r] = EDGE_INF;
+    __syncthreads();
+    const u32 j = c0 + 128 * w + 4 * lane;   // this lane's first column (n % 4 == 0)
+    const bool live = j < n;
+    const u32 imax = min(n, i0 + RS_ROWS);
+    // does any of this warp's columns need the j > i mask?
+    const bool mask = (c0 + 128 * w) <= (imax - 1);
+    u64 cm0 = EDGE_INF, cm1 = EDGE_INF, cm2 = EDGE_INF, cm3 = EDGE_INF;
+    for (u32 pass = 0; pass < RS_ROWS / 32; ++pass) {
+        const u32 ib = i0 + 32 * pass;
+        if (ib >= imax)
+            break;
+#pragma unroll 8
+        for (u32 r = 0; r < 32; ++r) {
+            const u32 i = ib + r;
+            u64 rp = EDGE_INF;
+            if (live && i < imax) {
+                const uint4 v = ld_stream_v4(W + (size_t)i * n + j);
+                const u32 k0 = key_of(v.x, DT), k1 = key_of(v.y, DT), k2 = key_of(v.z, DT),
+                          k3 = key_of(v.w, DT);
+                const u64 e0 = ((u64)k0 << 32) | j, e1 = ((u64)k1 << 32) | (j + 1);
+                const u64 e2 = ((u64)k2 << 32) | (j + 2), e3 = ((u64)k3 << 32) | (j + 3);
+                const u64 f0 = ((u64)k0 << 32) | i, f1 = ((u64)k1 << 32) | i;
+                const u64 f2 = ((u64)k2 << 32) | i, f3 = ((u64)k3 << 32) | i;
+                const bool ok0 = !mask || j > i, ok1 = !mask || j + 1 > i;
+                const bool ok2 = !mask || j + 2 > i, ok3 = !mask || j + 3 > i;
+                if (ok0) { rp = e0 < rp ? e0 : rp; cm0 = f0 < cm0 ? f0 : cm0; }
+                if (ok1) { rp = e1 < rp ? e1 : rp; cm1 = f1 < cm1 ? f1 : cm1; }
+                if (ok2) { rp = e2 < rp ? e2 : rp; cm2 = f2 < cm2 ? f2 : cm2; }
+                if (ok3) { rp = e3 < rp ? e3 : rp; cm3 = f3 < cm3 ? f3 : cm3; }
+            }
+            // warp minimum of (key, column) for row i: smallest key, then the
+            // smallest column among the lanes holding it
+            const u32 rk = (u32)(rp >> 32);
+            const u32 kmin = __reduce_min_sync(0xFFFFFFFFu, rk);
+            const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, rk == kmin ? (u32)rp : 0xFFFFFFFFu);
+            if (lane == (r & 31) && jmin != 0xFFFFFFFFu)
+                atomicMin(&s_row[32 * pass + r], ((u64)kmin << 32) | jmin);
+        }
+    }
+    // column candidates: edge (i, j) with i the smallest-key row (ties: lower i)
+    if (live) {
+        if (cm0 != EDGE_INF) atomicMin(&best[j], pack_edge((u32)(cm0 >> 32), (u32)cm0, j));
+        if (cm1 != EDGE_INF) atomicMin(&best[j + 1], pack_edge((u32)(cm1 >> 32), (u32)cm1, j + 1));
+        if (cm2 != EDGE_INF) atomicMin(&best[j + 2], pack_edge((u32)(cm2 >> 32), (u32)cm2, j + 2));
+        if (cm3 != EDGE_INF) atomicMin(&best[j + 3], pack_edge((u32)(cm3 >> 32), (u32)cm3, j + 3));
+    }
+    __syncthreads();
+    for (u32 r = threadIdx.x; r < RS_ROWS && i0 + r < n; r += blockDim.x) {
+        u64 x = s_row[r];
+        if (x != EDGE_INF)
+            atomicMin(&best[i0 + r], pack_edge((u32)(x >> 32), i0 + r, (u32)x));
+    }
+}
+
 // --------------------------------------------------- Boruvka step (K2)
 struct StepArgs {
     int level;
@@ -234,11 +308,163 @@ struct ContractArgs {
     u32 bin_cap;
 };
 
-// Loads the rows of one work item and reduces each column over them.
-// Level 0 reads W (4-byte weights) and builds packed edges; later levels
-// read packed u64 entries of C_r.
+// Column work of one contraction item with NR rows of W (level 0).  rows[]
+// holds the item's rows in ascending order, so within a column "first
+// strictly smaller key" is the packed-edge order.  U column groups are loaded
+// before any is consumed, so that few-row items still keep enough 16-byte
+// loads in flight.
+template <int C>
+__device__ __forceinline__ u32 lane_of(const uint4& v)
+{
+    return C == 0 ? v.x : (C == 1 ? v.y : (C == 2 ? v.z : v.w));
+}
+
+// one column: the smallest key over the item's rows (first strictly smaller
+// wins, rows ascending), packed with its endpoints, folded into bin L
+template <int DT, int NR, int C>
+__device__ __forceinline__ void column_w(const uint4* v, const u32* rid, u32 j, u32 L, u32 A, u32 b0,
+                                         u32 nb, u64* bins)
+{
+    const u32 rel = L - b0;
+    if (L == A || rel >= nb)
+        return;
+    u32 bk = key_of(lane_of<C>(v[0]), DT), bi = rid[0];
+#pragma unroll
+    for (int q = 1; q < NR; ++q) {
+        const u32 k = key_of(lane_of<C>(v[q]), DT);
+        if (k < bk) {
+            bk = k;
+            bi = rid[q];
+        }
+    }
+    const u64 e = pack_edge(bk, bi, j);
+    u64* slot = &bins[rel];
+    if (e < *slot)
+        atomicMin(slot, e);
+}
+
+template <int DT, bool VEC>
+__device__ __forceinline__ void contract_cols_w(const u32* __restrict__ Wp, u32 cr,
+                                                const u32* __restrict__ label,
+                                                const u32* __restrict__ srows, u32 np, u32 A, u32 b0,
+                                                u32 nb, u64* bins)
+{
+    // up to 4 rows per pass; rows past np repeat row 0 (same key and row, so
+    // they never change a column's minimum) without being loaded again
+    constexpr int NR = 4, U = 1;
+    const u32 tid = threadIdx.x, bd = blockDim.x;
+    u32 rid[NR];
+    const u32* rp[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        rid[q] = srows[(u32)q < np ? q : 0];
+        rp[q] = Wp + (size_t)rid[q] * cr;
+    }
+    u32 jt = 0;
+    if (VEC) {
+        const u32 n4 = cr >> 2;
+        for (u32 g0 = tid; g0 < n4; g0 += U * bd) {
+            uint4 v[U][NR];
+            uint4 lab[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const u32 g = g0 + u * bd;
+                if (g < n4) {
+                    v[u][0] = ld_stream_v4(rp[0] + 4 * g);
+#pragma unroll
+                    for (int q = 1; q < NR; ++q)
+                        v[u][q] = ((u32)q < np) ? ld_stream_v4(rp[q] + 4 * g) : v[u][0];
+                    lab[u] = *reinterpret_cast<const uint4*>(label + 4 * g);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const u32 g = g0 + u * bd;
+                if (g < n4) {
+                    column_w<DT, NR, 0>(v[u], rid, 4 * g, lab[u].x, A, b0, nb, bins);
+                    column_w<DT, NR, 1>(v[u], rid, 4 * g + 1, lab[u].y, A, b0, nb, bins);
+                    column_w<DT, NR, 2>(v[u], rid, 4 * g + 2, lab[u].z, A, b0, nb, bins);
+                    column_w<DT, NR, 3>(v[u], rid, 4 * g + 3, lab[u].w, A, b0, nb, bins);
+                }
+            }
+        }
+        jt = 4 * n4;
+    }
+    for (u32 j = jt + tid; j < cr; j += bd) {
+        uint4 x[NR];
+        x[0].x = ld_stream_u32(rp[0] + j);
+#pragma unroll
+        for (int q = 1; q < NR; ++q)
+            x[q].x = ((u32)q < np) ? ld_stream_u32(rp[q] + j) : x[0].x;
+        column_w<DT, NR, 0>(x, rid, j, label[j], A, b0, nb, bins);
+    }
+}
+
+// Column work of one item pass of up to 4 rows of C_r (levels >= 1):
+// entries are packed edges already, so a column reduces by a plain minimum.
+__device__ __forceinline__ void contract_cols_c(const u64* __restrict__ Cp, u32 cr,
+                                                const u32* __restrict__ label,
+                                                const u32* __restrict__ srows, u32 np, u32 A, u32 b0,
+                                                u32 nb, u64* bins)
+{
+    constexpr int NR = 4;
+    const u32 tid = threadIdx.x, bd = blockDim.x;
+    const u64* rp[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+        rp[q] = Cp + (size_t)srows[(u32)q < np ? q : 0] * cr;
+    auto update = [&](u32 L, u64 e) {
+        u32 rel = L - b0;
+        if (L != A && rel < nb) {
+            u64* slot = &bins[rel];
+            if (e < *slot)
+                atomicMin(slot, e);
+        }
+    };
+    u32 jt = 0;
+    if (((cr & 1u) == 0) && (((uintptr_t)Cp & 15u) == 0)) {
+        const u32 n2 = cr >> 1;
+        for (u32 g = tid; g < n2; g += bd) {
+            uint4 v[NR];
+            v[0] = ld_stream_v4(rp[0] + 2 * g);
+#pragma unroll
+            for (int q = 1; q < NR; ++q)
+                v[q] = ((u32)q < np) ? ld_stream_v4(rp[q] + 2 * g) : v[0];
+            const uint2 lab = *reinterpret_cast<const uint2*>(label + 2 * g);
+            u64 e0 = EDGE_INF, e1 = EDGE_INF;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                u64 x0 = ((u64)v[q].y << 32) | v[q].x;
+                u64 x1 = ((u64)v[q].w << 32) | v[q].z;
+                e0 = x0 < e0 ? x0 : e0;
+                e1 = x1 < e1 ? x1 : e1;
+            }
+            update(lab.x, e0);
+            update(lab.y, e1);
+        }
+        jt = 2 * n2;
+    }
+    for (u32 j = jt + tid; j < cr; j += bd) {
+        u64 e = rp[0][j];
+#pragma unroll
+        for (int q = 1; q < NR; ++q) {
+            if ((u32)q < np) {
+                u64 x = rp[q][j];
+                e = x < e ? x : e;
+            }
+        }
+        update(label[j], e);
+    }
+}
+
+// Work loop of the contraction: each CTA takes items (a group A, a chunk of
+// at most CONTRACT_ROWS of its rows, a range of bins), reduces every column
+// of those rows into shared-memory bins indexed by the column's new
+// component, and writes the bins as row A of C_{r+1} (plain stores when one
+// item covers the group, atomic minima otherwise) together with the row's
+// minimum, the next round's best edge of A.
 template <int DT, int LEVEL0, bool VEC>
-__global__ void __launch_bounds__(1024, 1) k_contract(ContractArgs a)
+__global__ void __launch_bounds__(CONTRACT_THREADS, 1) k_contract(ContractArgs a)
 {
     extern __shared__ __align__(16) u64 bins[];
     __shared__ u32 s_item, s_rows[CONTRACT_ROWS];
@@ -276,7 +502,6 @@ __global__ void __launch_bounds__(1024, 1) k_contract(ContractArgs a)
             bins[b] = EDGE_INF;
         __syncthreads();
         if (LEVEL0 && tid == 0) {
-            // ascending row order makes "first strictly smaller" = packed order
             for (u32 i = 1; i < nrows; ++i) {
                 u32 v = s_rows[i], j = i;
                 while (j > 0 && s_rows[j - 1] > v) {
@@ -287,120 +512,14 @@ __global__ void __launch_bounds__(1024, 1) k_contract(ContractArgs a)
             }
         }
         __syncthreads();
-        u32 rows[CONTRACT_ROWS];
-#pragma unroll
-        for (int q = 0; q < CONTRACT_ROWS; ++q)
-            rows[q] = (q < (int)nrows) ? s_rows[q] : s_rows[0];
-
-        auto update = [&](u32 L, u64 e) {
-            u32 rel = L - b0;
-            if (L != A && rel < nb) {
-                u64* slot = &bins[rel];
-                if (e < *slot)
-                    atomicMin(slot, e);
-            }
-        };
-
-        if (LEVEL0) {
-            const u32* Wp = (const u32*)a.cin;
-            auto column = [&](const u32* v, u32 j, u32 L) {
-                if (L == A || (L - b0) >= nb)
-                    return;
-                u32 bk = key_of(v[0], DT), bi = 0;
-#pragma unroll
-                for (int q = 1; q < CONTRACT_ROWS; ++q) {
-                    if (q < (int)nrows) {
-                        u32 kk = key_of(v[q], DT);
-                        if (kk < bk) {
-                            bk = kk;
-                            bi = q;
-                        }
-                    }
-                }
-                update(L, pack_edge(bk, s_rows[bi], j));
-            };
-            if (VEC) {
-                const u32 n4 = cr >> 2;
-                for (u32 g = tid; g < n4; g += bd) {
-                    uint4 v[CONTRACT_ROWS];
-#pragma unroll
-                    for (int q = 0; q < CONTRACT_ROWS; ++q)
-                        if (q < (int)nrows)
-                            v[q] = ld_stream_v4(Wp + (size_t)rows[q] * cr + 4 * g);
-                    uint4 lab = *(const uint4*)(a.label + 4 * g);
-                    u32 col[CONTRACT_ROWS];
-#pragma unroll
-                    for (int q = 0; q < CONTRACT_ROWS; ++q)
-                        col[q] = v[q].x;
-                    column(col, 4 * g, lab.x);
-#pragma unroll
-                    for (int q = 0; q < CONTRACT_ROWS; ++q)
-                        col[q] = v[q].y;
-                    column(col, 4 * g + 1, lab.y);
-#pragma unroll
-                    for (int q = 0; q < CONTRACT_ROWS; ++q)
-                        col[q] = v[q].z;
-                    column(col, 4 * g + 2, lab.z);
-#pragma unroll
-                    for (int q = 0; q < CONTRACT_ROWS; ++q)
-                        col[q] = v[q].w;
-                    column(col, 4 * g + 3, lab.w);
-                }
-                for (u32 j = 4 * n4 + tid; j < cr; j += bd) {
-                    u32 col[CONTRACT_ROWS];
-#pragma unroll
-                    for (int q = 0; q < CONTRACT_ROWS; ++q)
-                        col[q] = (q < (int)nrows) ? Wp[(size_t)rows[q] * cr + j] : 0u;
-                    column(col, j, a.label[j]);
-                }
-            } else {
-                for (u32 j = tid; j < cr; j += bd) {
-                    u32 col[CONTRACT_ROWS];
-#pragma unroll
-                    for (int q = 0; q < CONTRACT_ROWS; ++q)
-                        col[q] = (q < (int)nrows) ? ld_stream_u32(Wp + (size_t)rows[q] * cr + j) : 0u;
-                    column(col, j, a.label[j]);
-                }
-            }
-        } else {
-            const u64* Cp = (const u64*)a.cin;
-            const bool vec2 = ((cr & 1u) == 0) && (((uintptr_t)Cp & 15u) == 0);
-            u32 jstart = 0;
-            if (vec2) {
-                const u32 n2 = cr >> 1;
-                for (u32 g = tid; g < n2; g += bd) {
-                    uint4 v[CONTRACT_ROWS];
-#pragma unroll
-                    for (int q = 0; q < CONTRACT_ROWS; ++q)
-                        if (q < (int)nrows)
-                            v[q] = ld_stream_v4(Cp + (size_t)rows[q] * cr + 2 * g);
-                    uint2 lab = *(const uint2*)(a.label + 2 * g);
-                    u64 e0 = EDGE_INF, e1 = EDGE_INF;
-#pragma unroll
-                    for (int q = 0; q < CONTRACT_ROWS; ++q) {
-                        if (q < (int)nrows) {
-                            u64 x0 = ((u64)v[q].y << 32) | v[q].x;
-                            u64 x1 = ((u64)v[q].w << 32) | v[q].z;
-                            e0 = x0 < e0 ? x0 : e0;
-                            e1 = x1 < e1 ? x1 : e1;
-                        }
-                    }
-                    update(lab.x, e0);
-                    update(lab.y, e1);
-                }
-                jstart = 2 * n2;
-            }
-            for (u32 j = jstart + tid; j < cr; j += bd) {
-                u64 e = EDGE_INF;
-#pragma unroll
-                for (int q = 0; q < CONTRACT_ROWS; ++q) {
-                    if (q < (int)nrows) {
-                        u64 x = Cp[(size_t)rows[q] * cr + j];
-                        e = x < e ? x : e;
-                    }
-                }
-                update(a.label[j], e);
-            }
+        // rows in passes of at most 4 (register budget); bins merge passes
+        for (u32 p0 = 0; p0 < nrows; p0 += 4) {
+            const u32 np = min(4u, nrows - p0);
+            if (LEVEL0)
+                contract_cols_w<DT, VEC>((const u32*)a.cin, cr, a.label, s_rows + p0, np, A, b0, nb,
+                                         bins);
+            else
+                contract_cols_c((const u64*)a.cin, cr, a.label, s_rows + p0, np, A, b0, nb, bins);
         }
         __syncthreads();
         // write row A of C_{r+1} (this bin range) and fold the row minimum
@@ -472,21 +591,25 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
     const bool vec = (n % 4 == 0) && ((uintptr_t)W % 16 == 0);
     prof_launches(1);
     prof_begin(PH_ROWMIN, s);
-    {
+    if (vec) {
+        // upper-triangle tiles; best[] is reduced with atomic minima from +inf
+        if ((err = cudaMemsetAsync(ws.best[0], 0xFF, (size_t)n * sizeof(u64), s)) != cudaSuccess)
+            return err;
+        dim3 grid((n + RS_COLS - 1) / RS_COLS, (n + RS_ROWS - 1) / RS_ROWS);
+        if (dt == 0)
+            k_rowmin_sym<0><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+        else
+            k_rowmin_sym<1><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+        if ((err = cudaGetLastError()) != cudaSuccess)
+            return err;
+    } else {
         int grid = ws.sms * 8;
         if (grid > (int)n)
             grid = (int)n;
-        if (dt == 0) {
-            if (vec)
-                k_rowmin<0, true><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
-            else
-                k_rowmin<0, false><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
-        } else {
-            if (vec)
-                k_rowmin<1, true><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
-            else
-                k_rowmin<1, false><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
-        }
+        if (dt == 0)
+            k_rowmin<0, false><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+        else
+            k_rowmin<1, false><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
         if ((err = cudaGetLastError()) != cudaSuccess)
             return err;
     }
@@ -557,7 +680,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         ca.item_group = ws.item_group;
         ca.ctr = ws.ctr;
         ca.bin_cap = ws.bin_cap;
-        dim3 grid(ws.contract_blocks), block(1024);
+        dim3 grid(ws.contract_blocks), block(CONTRACT_THREADS);
         const int ph = (r == 0) ? PH_CONTRACT0 : PH_CONTRACT;
         prof_begin(ph, s);
         if (r == 0)
