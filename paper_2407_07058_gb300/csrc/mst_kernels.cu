@@ -108,32 +108,41 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
         const u32 ib = i0 + 32 * pass;
         if (ib >= imax)
             break;
-#pragma unroll 8
-        for (u32 r = 0; r < 32; ++r) {
-            const u32 i = ib + r;
-            u64 rp = EDGE_INF;
-            if (live && i < imax) {
-                const uint4 v = ld_stream_v4(W + (size_t)i * n + j);
-                const u32 k0 = key_of(v.x, DT), k1 = key_of(v.y, DT), k2 = key_of(v.z, DT),
-                          k3 = key_of(v.w, DT);
-                const u64 e0 = ((u64)k0 << 32) | j, e1 = ((u64)k1 << 32) | (j + 1);
-                const u64 e2 = ((u64)k2 << 32) | (j + 2), e3 = ((u64)k3 << 32) | (j + 3);
-                const u64 f0 = ((u64)k0 << 32) | i, f1 = ((u64)k1 << 32) | i;
-                const u64 f2 = ((u64)k2 << 32) | i, f3 = ((u64)k3 << 32) | i;
-                const bool ok0 = !mask || j > i, ok1 = !mask || j + 1 > i;
-                const bool ok2 = !mask || j + 2 > i, ok3 = !mask || j + 3 > i;
-                if (ok0) { rp = e0 < rp ? e0 : rp; cm0 = f0 < cm0 ? f0 : cm0; }
-                if (ok1) { rp = e1 < rp ? e1 : rp; cm1 = f1 < cm1 ? f1 : cm1; }
-                if (ok2) { rp = e2 < rp ? e2 : rp; cm2 = f2 < cm2 ? f2 : cm2; }
-                if (ok3) { rp = e3 < rp ? e3 : rp; cm3 = f3 < cm3 ? f3 : cm3; }
+        for (u32 r8 = 0; r8 < 32; r8 += 8) {
+            // issue eight rows' loads before consuming any (memory-level parallelism)
+            uint4 v[8];
+#pragma unroll
+            for (u32 q = 0; q < 8; ++q) {
+                const u32 i = ib + r8 + q;
+                if (live && i < imax)
+                    v[q] = ld_stream_v4(W + (size_t)i * n + j);
             }
-            // warp minimum of (key, column) for row i: smallest key, then the
-            // smallest column among the lanes holding it
-            const u32 rk = (u32)(rp >> 32);
-            const u32 kmin = __reduce_min_sync(0xFFFFFFFFu, rk);
-            const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, rk == kmin ? (u32)rp : 0xFFFFFFFFu);
-            if (lane == (r & 31) && jmin != 0xFFFFFFFFu)
-                atomicMin(&s_row[32 * pass + r], ((u64)kmin << 32) | jmin);
+#pragma unroll
+            for (u32 q = 0; q < 8; ++q) {
+                const u32 r = r8 + q, i = ib + r;
+                u64 rp = EDGE_INF;
+                if (live && i < imax) {
+                    const u32 k0 = key_of(v[q].x, DT), k1 = key_of(v[q].y, DT);
+                    const u32 k2 = key_of(v[q].z, DT), k3 = key_of(v[q].w, DT);
+                    const u64 e0 = ((u64)k0 << 32) | j, e1 = ((u64)k1 << 32) | (j + 1);
+                    const u64 e2 = ((u64)k2 << 32) | (j + 2), e3 = ((u64)k3 << 32) | (j + 3);
+                    const u64 f0 = ((u64)k0 << 32) | i, f1 = ((u64)k1 << 32) | i;
+                    const u64 f2 = ((u64)k2 << 32) | i, f3 = ((u64)k3 << 32) | i;
+                    const bool ok0 = !mask || j > i, ok1 = !mask || j + 1 > i;
+                    const bool ok2 = !mask || j + 2 > i, ok3 = !mask || j + 3 > i;
+                    if (ok0) { rp = e0 < rp ? e0 : rp; cm0 = f0 < cm0 ? f0 : cm0; }
+                    if (ok1) { rp = e1 < rp ? e1 : rp; cm1 = f1 < cm1 ? f1 : cm1; }
+                    if (ok2) { rp = e2 < rp ? e2 : rp; cm2 = f2 < cm2 ? f2 : cm2; }
+                    if (ok3) { rp = e3 < rp ? e3 : rp; cm3 = f3 < cm3 ? f3 : cm3; }
+                }
+                // warp minimum of (key, column) for row i: smallest key, then the
+                // smallest column among the lanes holding it
+                const u32 rk = (u32)(rp >> 32);
+                const u32 kmin = __reduce_min_sync(0xFFFFFFFFu, rk);
+                const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, rk == kmin ? (u32)rp : 0xFFFFFFFFu);
+                if (lane == r && jmin != 0xFFFFFFFFu)
+                    atomicMin(&s_row[32 * pass + r], ((u64)kmin << 32) | jmin);
+            }
         }
     }
     // column candidates: edge (i, j) with i the smallest-key row (ties: lower i)
@@ -343,6 +352,45 @@ __device__ __forceinline__ void column_w(const uint4* v, const u32* rid, u32 j, 
         atomicMin(slot, e);
 }
 
+// Folds the 4 columns of one group (columns j..j+3, labels lab) into the
+// bins.  All four bins are read before any atomic: a stale read can only
+// cause a redundant atomicMin, never a lost update, and the four shared
+// loads then overlap instead of forming one dependent chain.
+template <int DT, int NP, bool ONE>
+__device__ __forceinline__ void fold_group(const uint4* x, const u32* rid, u32 j, uint4 lab, u32 A,
+                                           u32 b0, u32 nb, u64* bins)
+{
+    u32 L[4] = {lab.x, lab.y, lab.z, lab.w};
+    u64 e[4];
+    u32 rel[4];
+    bool ok[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        rel[c] = ONE ? L[c] : L[c] - b0;
+        ok[c] = (L[c] != A) && (ONE || rel[c] < nb);
+        u32 v0 = c == 0 ? x[0].x : (c == 1 ? x[0].y : (c == 2 ? x[0].z : x[0].w));
+        u32 bk = key_of(v0, DT), bi = rid[0];
+#pragma unroll
+        for (int q = 1; q < NP; ++q) {
+            u32 vq = c == 0 ? x[q].x : (c == 1 ? x[q].y : (c == 2 ? x[q].z : x[q].w));
+            const u32 k = key_of(vq, DT);
+            if (k < bk) {
+                bk = k;
+                bi = rid[q];
+            }
+        }
+        e[c] = pack_edge(bk, bi, j + c);
+    }
+    u64 cur[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        cur[c] = ok[c] ? bins[rel[c]] : 0ull;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (ok[c] && e[c] < cur[c])
+            atomicMin(&bins[rel[c]], e[c]);
+}
+
 template <int DT, bool VEC>
 __device__ __forceinline__ void contract_cols_w(const u32* __restrict__ Wp, u32 cr,
                                                 const u32* __restrict__ label,
@@ -380,12 +428,8 @@ __device__ __forceinline__ void contract_cols_w(const u32* __restrict__ Wp, u32 
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const u32 g = g0 + u * bd;
-                if (g < n4) {
-                    column_w<DT, NR, 0>(v[u], rid, 4 * g, lab[u].x, A, b0, nb, bins);
-                    column_w<DT, NR, 1>(v[u], rid, 4 * g + 1, lab[u].y, A, b0, nb, bins);
-                    column_w<DT, NR, 2>(v[u], rid, 4 * g + 2, lab[u].z, A, b0, nb, bins);
-                    column_w<DT, NR, 3>(v[u], rid, 4 * g + 3, lab[u].w, A, b0, nb, bins);
-                }
+                if (g < n4)
+                    fold_group<DT, NR, false>(v[u], rid, 4 * g, lab[u], A, b0, nb, bins);
             }
         }
         jt = 4 * n4;
@@ -625,6 +669,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
     const size_t smem = (size_t)ws.bin_cap * sizeof(u64);
     auto k0 = (dt == 0) ? (vec ? k_contract<0, 1, true> : k_contract<0, 1, false>)
                         : (vec ? k_contract<1, 1, true> : k_contract<1, 1, false>);
+
     auto k1 = k_contract<0, 0, false>;
     if ((err = set_smem(k0, smem)) != cudaSuccess)
         return err;
