@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--workload", default="big", choices=sorted(WORKLOADS))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
     return p.parse_args()
 
 
@@ -183,6 +184,56 @@ def cpu_baseline(kind: str, n_full: int, budget_s: float = 12.0):
     return {"value": runs * n * n / total, "unit": "entries/s", "cores": 1, "kind": "oracle",
             "sample": f"n={n} graph from the same distribution, {runs} run(s), "
                       f"{total:.1f} s total, Prim + Algorithm 4, one thread"}
+
+
+def bench_batched(steps: int, warmup: int, dev):
+    """4096 graphs, n = floor(32 * 64^u) clipped to [32, 2048], FP32 uniform(0,1)
+    weights seeded per graph: one batched call vs 4096 plain solves."""
+    import torch
+
+    import synth
+    from paper_2407_07058_gb300 import appd
+    sizes = [int(x) for x in synth.cfg4_sizes(4096)]
+    offs = np.cumsum([0] + [n * n for n in sizes])[:-1].astype(np.int64)
+    total = int(offs[-1] + sizes[-1] ** 2)
+    W = torch.empty(total, dtype=torch.float32, device=dev)
+    M = torch.empty_like(W)
+    st = torch.cuda.current_stream()
+    for g, n in enumerate(sizes):
+        synth.device_uniform01(synth.cfg4_seed(g), n, W.data_ptr() + 4 * int(offs[g]), st.cuda_stream)
+    torch.cuda.synchronize()
+    for _ in range(max(1, warmup)):
+        appd.solve_batched(W, offs, sizes, out=M)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    appd.profile_begin()
+    e0.record(st)
+    for _ in range(steps):
+        appd.solve_batched(W, offs, sizes, out=M)
+    e1.record(st)
+    torch.cuda.synchronize()
+    prof = appd.profile_end()
+    ms_b = e0.elapsed_time(e1) / steps
+    # one by one: 4096 plain solves on the same stream
+    views = [(W[o: o + n * n].view(n, n), M[o: o + n * n].view(n, n)) for o, n in zip(offs, sizes)]
+    for w, m in views[:64]:
+        appd.solve(w, out=m)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for w, m in views:
+        appd.solve(w, out=m)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_1 = e0.elapsed_time(e1)
+    if appd.last_device_status() != 0:
+        raise RuntimeError("device status error in the batched run")
+    ent = float(sum(n * n for n in sizes))
+    return {"workload": "4096 graphs, n log-uniform in [32, 2048], FP32 uniform(0,1) weights",
+            "graphs": len(sizes), "ms_per_batch": ms_b, "graphs_per_s": len(sizes) / (ms_b / 1e3),
+            "entries_per_s": ent / (ms_b / 1e3),
+            "one_by_one_ms": ms_1, "one_by_one_graphs_per_s": len(sizes) / (ms_1 / 1e3),
+            "speedup_vs_one_by_one": ms_1 / ms_b, "kernel_launches_per_batch": prof["launches"] / steps,
+            "bytes_w_plus_m": 8.0 * ent}
 
 
 # ------------------------------------------------------------------ arms
@@ -321,6 +372,11 @@ def run_ours(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(kind, n)
+    batched = None
+    if not args.no_batched:
+        del W, M
+        torch.cuda.empty_cache()
+        batched = bench_batched(max(3, min(args.steps, 10)), args.warmup, dev)
 
     if rank == 0:
         line = {
@@ -338,6 +394,7 @@ def run_ours(args, rank, world, local):
             "phases_ms_per_step": {k: prof[k] / args.steps for k in appd.PHASES},
             "c1": c1,
             "hbm_frac_solve_design_bytes": solve_frac,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

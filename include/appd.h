@@ -148,6 +148,16 @@ appd_status appd_solve_batched(const int64_t *offsets, const void *Ws, const int
                                const uint8_t *dts, void *Ms, int32_t count, appd_stream_t s);
 
 /*
+ * appd_batched_tuning -- sets the batched path's parameters for this process:
+ *   ctas_per_sm  persistent CTAs per SM (1 or 2), each with its own workspace;
+ *   fill_rows    rows per fill tile inside a CTA (64, 128, 256 or 512);
+ *   n_split      graphs with n > n_split go through the single-solve pipeline.
+ * Defaults: 1, 256, 2048.  Returns APPD_ERR_INVALID for values out of range.
+ * (No counterpart in the paper: scheduling parameters of this library.)
+ */
+appd_status appd_batched_tuning(int32_t ctas_per_sm, int32_t fill_rows, int64_t n_split);
+
+/*
  * appd_check_symmetric -- returns APPD_OK if W(i,j) and W(j,i) have identical
  * bits for all i < j, APPD_ERR_ASYMMETRIC otherwise.  Synchronizes s.
  */
@@ -172,7 +182,8 @@ appd_status appd_release_workspaces(void);
  * up to cap doubles to out: summed device milliseconds per phase
  *   [0] round-1 row minima   [1] Boruvka steps       [2] contraction of W
  *   [3] later contractions   [4] leaf order          [5] fill of M
- * then [6] kernels launched, [7] components after round 1 of the last solve.
+ *   [6] batched persistent kernel
+ * then [7] kernels launched, [8] components after round 1 of the last solve.
  * Returns the number of values written.
  */
 int32_t appd_profile_begin(void);

@@ -23,7 +23,7 @@ STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD
 
 # every symbol that include/appd.h declares
 EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host", "appd_mst",
-           "appd_leaf_order", "appd_solve_batched", "appd_check_symmetric",
+           "appd_leaf_order", "appd_solve_batched", "appd_batched_tuning", "appd_check_symmetric",
            "appd_last_device_status", "appd_release_workspaces", "appd_profile_begin",
            "appd_profile_end", "appd_server_create",
            "appd_server_submit", "appd_server_commit", "appd_server_poll", "appd_server_release",
@@ -57,6 +57,7 @@ def load(build_if_missing: bool = True):
             "appd_mst": [vp, i64, ci, vp, vp],
             "appd_leaf_order": [vp, i64, ci, vp, vp, vp],
             "appd_solve_batched": [vp, vp, vp, vp, vp, i32, vp],
+            "appd_batched_tuning": [i32, i32, i64],
             "appd_check_symmetric": [vp, i64, ci, vp],
             "appd_last_device_status": [vp],
             "appd_release_workspaces": [],
@@ -198,7 +199,7 @@ def last_device_status(stream=None) -> int:
     return int(load().appd_last_device_status(_stream_ptr(stream)))
 
 
-PHASES = ["rowmin", "boruvka_step", "contract_w", "contract_c", "leaf_order", "fill"]
+PHASES = ["rowmin", "boruvka_step", "contract_w", "contract_c", "leaf_order", "fill", "batched"]
 
 
 def profile_begin():
@@ -207,13 +208,17 @@ def profile_begin():
 
 def profile_end() -> dict:
     """Per-phase device ms since profile_begin, kernel launch count, c1."""
-    buf = (ctypes.c_double * 8)()
-    k = load().appd_profile_end(buf, 8)
+    buf = (ctypes.c_double * 9)()
+    k = load().appd_profile_end(buf, 9)
     vals = [buf[i] for i in range(k)]
     out = {name: vals[i] for i, name in enumerate(PHASES)}
-    out["launches"] = int(vals[6])
-    out["c1"] = int(vals[7])
+    out["launches"] = int(vals[7])
+    out["c1"] = int(vals[8])
     return out
+
+
+def batched_tuning(ctas_per_sm: int = 1, fill_rows: int = 256, n_split: int = 2048):
+    _check(load().appd_batched_tuning(ctas_per_sm, fill_rows, n_split), "appd_batched_tuning")
 
 
 def release_workspaces():

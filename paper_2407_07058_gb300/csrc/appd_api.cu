@@ -17,6 +17,7 @@ constexpr int MAX_DEV = 64;
 std::mutex g_mu;
 Workspace* g_ws[MAX_DEV] = {};
 u32* g_status[MAX_DEV] = {};
+BatchTuning g_tune;
 
 // ------------------------------------------------------------- profiling
 struct ProfMark {
@@ -51,9 +52,9 @@ appd_status cuda_fail(cudaError_t e)
     return APPD_ERR_CUDA;
 }
 
-// Carves the workspace arrays for capacity `cap` out of one allocation (or
-// only measures when base == nullptr).
-size_t carve(Workspace& w, char* base, int64_t cap)
+}  // namespace
+
+size_t appd::workspace_layout(Workspace& w, char* base, int64_t cap)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
@@ -93,6 +94,10 @@ size_t carve(Workspace& w, char* base, int64_t cap)
     w.st = (u32*)take((size_t)lv * N * sizeof(u32));
     return align_up(off, 256);
 }
+
+namespace {
+
+size_t carve(Workspace& w, char* base, int64_t cap) { return workspace_layout(w, base, cap); }
 
 // The device's workspace with capacity >= n (grown if needed).
 appd_status get_ws(int64_t n, Workspace** out)
@@ -497,13 +502,57 @@ appd_status appd_solve_batched(const int64_t* offsets, const void* Ws, const int
         if (dts && dts[g] != APPD_F32 && dts[g] != APPD_U32)
             return APPD_ERR_INVALID;
     }
+    if (Ws != Ms) {
+        for (int32_t g = 0; g < count; ++g) {
+            const u32* W = (const u32*)Ws + offsets[g];
+            const u32* M = (const u32*)Ms + offsets[g];
+            const size_t bytes = (size_t)ns[g] * (size_t)ns[g] * 4;
+            if ((const char*)W < (const char*)M + bytes && (const char*)M < (const char*)W + bytes)
+                return APPD_ERR_ALIAS;
+        }
+    }
+    BatchTuning tune;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        tune = g_tune;
+    }
+    std::vector<int32_t> small;
     for (int32_t g = 0; g < count; ++g) {
-        const u32* W = (const u32*)Ws + offsets[g];
-        u32* M = (u32*)Ms + offsets[g];
-        appd_status st = appd_solve(W, ns[g], dts ? (appd_dtype)dts[g] : APPD_F32, M, s);
-        if (st != APPD_OK)
+        if (ns[g] == 0)
+            continue;
+        if (ns[g] <= tune.n_split) {
+            small.push_back(g);
+        } else {
+            const u32* W = (const u32*)Ws + offsets[g];
+            u32* M = (u32*)Ms + offsets[g];
+            appd_status st = appd_solve(W, ns[g], dts ? (appd_dtype)dts[g] : APPD_F32, M, s);
+            if (st != APPD_OK)
+                return st;
+        }
+    }
+    if (small.empty())
+        return APPD_OK;
+    u32* status = nullptr;
+    appd_status st;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if ((st = get_status(&status)) != APPD_OK)
             return st;
     }
+    cudaError_t e = run_batched(offsets, Ws, ns, dts, Ms, small, tune, status, (cudaStream_t)s);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
+appd_status appd_batched_tuning(int32_t ctas_per_sm, int32_t fill_rows, int64_t n_split)
+{
+    if (ctas_per_sm < 1 || ctas_per_sm > 2 || (fill_rows != 64 && fill_rows != 128 &&
+                                               fill_rows != 256 && fill_rows != 512) ||
+        n_split < 1 || n_split > 65536)
+        return APPD_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune.ctas_per_sm = ctas_per_sm;
+    g_tune.fill_rows = fill_rows;
+    g_tune.n_split = n_split;
     return APPD_OK;
 }
 
@@ -580,6 +629,7 @@ appd_status appd_release_workspaces(void)
         delete g_ws[dev];
         g_ws[dev] = nullptr;
     }
+    release_batched_runtime();
     return APPD_OK;
 }
 

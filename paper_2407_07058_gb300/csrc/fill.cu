@@ -19,159 +19,18 @@
 // In the leaf order tree1 is [pos(nha(y)), pos(y)) and tree2 is
 // [pos(y), pos(y) + nsize(y)) for the edge above vertex y; the target cells
 // are scattered in M, which is what this form costs.
-#include "internal.h"
+#include "fill_device.cuh"
 
 namespace appd {
 
-constexpr int FC = 128;   // columns per CTA
-constexpr int FT = 256;   // threads per CTA
-
-__device__ __forceinline__ u32 rmq_gap(const u32* __restrict__ st, u32 stride, u32 a, u32 b)
-{
-    // max gap[a..b]; an empty range (only on an invalid order) gives 0
-    if (b < a)
-        return 0u;
-    u32 l = 31 - __clz(b - a + 1);
-    u32 x = __ldg(st + (size_t)l * stride + a);
-    u32 y = __ldg(st + (size_t)l * stride + b - (1u << l) + 1);
-    return x > y ? x : y;
-}
-
-// dynamic shared memory layout of k_fill
-struct FillSmem {
-    u32 T[FC + 1][FC];   // T[t][col]: running max of A outward from split t
-    u64 sort[FC];
-    u32 q[FC];           // sorted column positions
-    u32 col[FC];         // sorted index -> column offset
-    u32 rank[FC];        // column offset -> sorted index
-    u32 A[FC];           // A[k] = max gap between q[k] and q[k+1]
-};
-
-size_t fill_smem_bytes(u32 rows_per_cta) { return sizeof(FillSmem) + (size_t)rows_per_cta * 12; }
-
-// For a row with leaf position p, let t = #{sorted columns with q < p}.  Its
-// value at the column with sorted index k is max(R_p, A[t..k-1]) for k >= t
-// and max(L_p, A[k..t-2]) for k < t, where R_p / L_p are the largest gaps
-// from p to the nearest column on each side.  The A-parts depend only on
-// (t, k): they form the table T, built once per CTA, so each output element
-// costs one shared load, one max and the key-to-bits transform.
 template <int DT>
 __global__ void __launch_bounds__(FT, 2) k_fill(const u32* __restrict__ pos, const u32* __restrict__ st,
                                                 u32 n, u32 rows_per_cta, u32* __restrict__ M)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FillSmem& S = *reinterpret_cast<FillSmem*>(smem_raw);
-    u32* s_t = reinterpret_cast<u32*>(smem_raw + sizeof(FillSmem));
-    u32* s_L = s_t + rows_per_cta;
-    u32* s_R = s_L + rows_per_cta;
-
-    const u32 tid = threadIdx.x;
-    const u32 j0 = blockIdx.x * FC;
-    const u32 nc = min((u32)FC, n - j0);
     const u32 r0 = blockIdx.y * rows_per_cta;
-    const u32 nr = min(rows_per_cta, n - r0);
-
-    // 1. sort the tile's column positions (bitonic, FC elements)
-    if (tid < FC)
-        S.sort[tid] = ((u64)(tid < nc ? __ldg(pos + j0 + tid) : 0xFFFFFFFFu) << 32) | tid;
-    __syncthreads();
-    for (u32 k = 2; k <= FC; k <<= 1) {
-        for (u32 j = k >> 1; j > 0; j >>= 1) {
-            if (tid < FC) {
-                u32 ixj = tid ^ j;
-                if (ixj > tid) {
-                    bool up = (tid & k) == 0;
-                    u64 x = S.sort[tid], y = S.sort[ixj];
-                    if ((x > y) == up) {
-                        S.sort[tid] = y;
-                        S.sort[ixj] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (tid < FC) {
-        u64 e = S.sort[tid];
-        S.q[tid] = (u32)(e >> 32);
-        S.col[tid] = (u32)e;
-        if (tid < nc)
-            S.rank[(u32)e] = tid;
-    }
-    __syncthreads();
-    // 2. gaps between consecutive sorted columns; row split points and sides
-    if (tid + 1 < nc)
-        S.A[tid] = rmq_gap(st, n, S.q[tid], S.q[tid + 1] - 1);
-    for (u32 r = tid; r < nr; r += FT) {
-        u32 p = __ldg(pos + r0 + r);
-        u32 lo = 0, hi = nc;
-        while (lo < hi) {
-            u32 mid = (lo + hi) >> 1;
-            if (S.q[mid] < p)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        s_t[r] = lo;
-        s_L[r] = lo > 0 ? rmq_gap(st, n, S.q[lo - 1], p - 1) : 0u;
-        s_R[r] = (lo < nc && S.q[lo] != p) ? rmq_gap(st, n, p, S.q[lo] - 1) : 0u;
-    }
-    __syncthreads();
-    // 3. the table: row t holds the running maxima outward from split t
-    if (tid <= nc) {
-        const u32 t = tid;
-        u32 cur = 0;
-        for (u32 k = t; k < nc; ++k) {
-            if (k > t) {
-                u32 a = S.A[k - 1];
-                cur = cur > a ? cur : a;
-            }
-            S.T[t][S.col[k]] = cur;
-        }
-        cur = 0;
-        for (u32 k = t; k-- > 0;) {
-            if (k + 1 < t) {
-                u32 a = S.A[k];
-                cur = cur > a ? cur : a;
-            }
-            S.T[t][S.col[k]] = cur;
-        }
-    }
-    __syncthreads();
-    // 4. rows: one warp per row, each lane four consecutive columns
-    const u32 lane = tid & 31, w = tid >> 5;
-    const bool vec = (nc == FC) && (n % 4u) == 0 && (((uintptr_t)M & 15u) == 0);
-    if (vec) {
-        const u32 jj = 4 * lane;
-        const uint4 rk = *reinterpret_cast<const uint4*>(&S.rank[jj]);
-        for (u32 r = w; r < nr; r += FT / 32) {
-            const u32 t = s_t[r], L = s_L[r], R = s_R[r];
-            const uint4 tv = *reinterpret_cast<const uint4*>(&S.T[t][jj]);
-            u32 v0 = max(tv.x, rk.x >= t ? R : L);
-            u32 v1 = max(tv.y, rk.y >= t ? R : L);
-            u32 v2 = max(tv.z, rk.z >= t ? R : L);
-            u32 v3 = max(tv.w, rk.w >= t ? R : L);
-            uint4 o = make_uint4(bits_of(v0, DT), bits_of(v1, DT), bits_of(v2, DT), bits_of(v3, DT));
-            const u32 i = r0 + r;
-            const u32 dc = i - j0 - jj;     // the diagonal cell is all-zero bits
-            if (dc < 4u) {
-                if (dc == 0) o.x = 0u;
-                if (dc == 1) o.y = 0u;
-                if (dc == 2) o.z = 0u;
-                if (dc == 3) o.w = 0u;
-            }
-            __stcs(reinterpret_cast<uint4*>(M + (size_t)i * n + j0 + jj), o);
-        }
-    } else {
-        for (u32 r = w; r < nr; r += FT / 32) {
-            const u32 t = s_t[r], L = s_L[r], R = s_R[r];
-            const u32 i = r0 + r;
-            for (u32 c = lane; c < nc; c += 32) {
-                u32 v = max(S.T[t][c], S.rank[c] >= t ? R : L);
-                M[(size_t)i * n + j0 + c] = (j0 + c == i) ? 0u : bits_of(v, DT);
-            }
-        }
-    }
+    fill_tile<DT>(pos, st, n, blockIdx.x * FC, r0, min(rows_per_cta, n - r0), rows_per_cta, M,
+                  smem_raw);
 }
 
 // ----------------------------------------------------- Algorithm 4 form

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 #include "common.cuh"
 
@@ -84,10 +85,26 @@ cudaError_t run_fill_alg4(Workspace& ws, int dt, void* M, u32* status, cudaStrea
 cudaError_t run_fill_trivial(int64_t n, void* M, cudaStream_t s);   // n == 1
 
 // profiling (appd_profile_begin/end): phases of a solve
-enum Phase { PH_ROWMIN = 0, PH_STEP, PH_CONTRACT0, PH_CONTRACT, PH_LEAF, PH_FILL, PH_COUNT };
+enum Phase { PH_ROWMIN = 0, PH_STEP, PH_CONTRACT0, PH_CONTRACT, PH_LEAF, PH_FILL, PH_BATCHED, PH_COUNT };
 void prof_begin(int phase, cudaStream_t s);
 void prof_end(int phase, cudaStream_t s);
 void prof_launches(int k);
+
+// Carves the workspace arrays for capacity cap out of base (or only
+// measures when base is null); returns the bytes needed.
+size_t workspace_layout(Workspace& w, char* base, int64_t cap);
+
+// batched solves (batched.cu): graphs listed in `small` run one per CTA in
+// the persistent kernel
+struct BatchTuning {
+    int ctas_per_sm = 1;     // persistent CTAs per SM (one workspace slice each)
+    int fill_rows = 256;     // rows per fill tile inside a CTA
+    int64_t n_split = 2048;  // larger graphs use the single-solve pipeline
+};
+cudaError_t run_batched(const int64_t* offsets, const void* Ws, const int64_t* ns, const uint8_t* dts,
+                        void* Ms, const std::vector<int32_t>& small, const BatchTuning& tune,
+                        u32* status, cudaStream_t s);
+void release_batched_runtime();
 
 // sizes
 size_t contraction_scratch_bytes(int64_t n);

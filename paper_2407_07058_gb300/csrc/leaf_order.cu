@@ -21,330 +21,14 @@
 //   4. a sparse table over the gaps for O(1) range maxima.
 // All phases run in one cooperative kernel separated by bounded grid
 // barriers.
-#include "internal.h"
+#include "leaf_device.cuh"
 
 namespace appd {
-
-struct LeafArgs {
-    u32 n;
-    int levels;      // binary-lifting levels (>= 1)
-    int st_levels;   // sparse-table levels over n-1 gaps
-    const u64* mst;  // n-1 packed edges
-    u32 *deg, *adj_off, *afill, *adj, *aslot;
-    u32 *lr_d0, *lr_d1, *lr_nx0, *lr_nx1;
-    u32 *parent, *pe_key;
-    u64* ord;
-    u32* jump;
-    u64* mxo;
-    u32* nha;
-    u64 *skey0, *skey1;
-    u32* hist;
-    u32 ntiles;
-    u32 *first_child, *next_sib;
-    u32 *pos, *order, *nsize, *gap, *st;
-    u32* part;
-    Counters* ctr;
-    u32* status;
-};
-
-constexpr u32 LR_END = 0xFFFFFFFFu;
-constexpr int SORT_TILE = 2048;
-constexpr int SORT_NW = 16;   // warps of a 512-thread CTA
-
-// Wyllie list ranking: d[a] becomes the sum of weights from a to the end of
-// its list (inclusive).  Returns the buffer index that holds the result.
-__device__ int list_rank(const GridTeam& t, u32 na, u32* d0, u32* d1, u32* x0, u32* x1,
-                         int rounds, bool* ok)
-{
-    u32 *dc = d0, *dn = d1, *xc = x0, *xn = x1;
-    int cur = 0;
-    for (int it = 0; it < rounds; ++it) {
-        for (u32 a = t.rank(); a < na; a += t.size()) {
-            u32 nx = xc[a];
-            if (nx != LR_END) {
-                dn[a] = dc[a] + dc[nx];
-                xn[a] = xc[nx];
-            } else {
-                dn[a] = dc[a];
-                xn[a] = LR_END;
-            }
-        }
-        if (!t.sync()) {
-            *ok = false;
-            return cur;
-        }
-        u32* tmp = dc;
-        dc = dn;
-        dn = tmp;
-        tmp = xc;
-        xc = xn;
-        xn = tmp;
-        cur ^= 1;
-    }
-    *ok = true;
-    return cur;
-}
 
 __global__ void __launch_bounds__(512) k_leaf_order(LeafArgs a)
 {
     GridTeam t{&a.ctr->bar, a.status};
-    const u32 n = a.n, m = n - 1, na = 2 * m;
-    const u32 me = t.rank(), ts = t.size();
-    __shared__ u32 s_cnt[256];
-    __shared__ u32 s_off[256];
-    __shared__ u32 s_wc[SORT_NW][256];
-
-    // ---- adjacency of the MST
-    for (u32 v = me; v < n; v += ts) {
-        a.deg[v] = 0;
-        a.afill[v] = 0;
-        a.first_child[v] = NONE32;
-    }
-    if (!t.sync())
-        return;
-    for (u32 e = me; e < m; e += ts) {
-        u64 x = a.mst[e];
-        atomicAdd(&a.deg[edge_lo(x)], 1u);
-        atomicAdd(&a.deg[edge_hi(x)], 1u);
-    }
-    if (!t.sync())
-        return;
-    u32 tot = 0;
-    if (!team_excl_scan(t, a.deg, a.adj_off, n, a.part, &tot))
-        return;
-    if (!t.sync())
-        return;
-    for (u32 e = me; e < m; e += ts) {
-        u64 x = a.mst[e];
-        u32 lo = edge_lo(x), hi = edge_hi(x);
-        u32 s0 = atomicAdd(&a.afill[lo], 1u);
-        a.adj[a.adj_off[lo] + s0] = 2 * e;       // arc lo -> hi
-        a.aslot[2 * e] = s0;
-        u32 s1 = atomicAdd(&a.afill[hi], 1u);
-        a.adj[a.adj_off[hi] + s1] = 2 * e + 1;   // arc hi -> lo
-        a.aslot[2 * e + 1] = s1;
-    }
-    if (!t.sync())
-        return;
-    // ---- Euler tour successor of every arc; the tour starts at vertex 0
-    const u32 first = a.adj[a.adj_off[0]];
-    for (u32 x = me; x < na; x += ts) {
-        u64 e = a.mst[x >> 1];
-        u32 dst = (x & 1) ? edge_lo(e) : edge_hi(e);
-        u32 sl = a.aslot[x ^ 1u] + 1;
-        if (sl == a.deg[dst])
-            sl = 0;
-        u32 nx = a.adj[a.adj_off[dst] + sl];
-        if (nx == first)
-            nx = LR_END;
-        a.lr_nx0[x] = nx;
-        a.lr_d0[x] = (nx == LR_END) ? 0u : 1u;
-    }
-    if (!t.sync())
-        return;
-    bool ok = true;
-    int rounds = ceil_log2_dev(na) + 1;
-    int which = list_rank(t, na, a.lr_d0, a.lr_d1, a.lr_nx0, a.lr_nx1, rounds, &ok);
-    if (!ok)
-        return;
-    const u32* dist = which ? a.lr_d1 : a.lr_d0;   // arcs after this one
-    // ---- orientation: the earlier arc of an edge goes down the tree
-    for (u32 e = me; e < m; e += ts) {
-        u64 x = a.mst[e];
-        u32 lo = edge_lo(x), hi = edge_hi(x), key = edge_key(x);
-        bool down_lo_hi = dist[2 * e] > dist[2 * e + 1];   // more arcs after it == earlier
-        u32 child = down_lo_hi ? hi : lo, par = down_lo_hi ? lo : hi;
-        a.parent[child] = par;
-        a.pe_key[child] = key;
-        a.ord[child] = ((u64)key << 16) | child;
-    }
-    if (me == 0) {
-        a.parent[0] = 0;
-        a.pe_key[0] = 0;
-        a.ord[0] = EDGE_INF;
-    }
-    if (!t.sync())
-        return;
-    // ---- binary lifting: jump[k][v] = 2^k-th ancestor, mxo[k][v] = max ord
-    // over v and its next 2^k - 1 ancestors (the root's ord is infinite)
-    for (u32 v = me; v < n; v += ts) {
-        a.jump[v] = a.parent[v];
-        a.mxo[v] = a.ord[v];
-    }
-    if (!t.sync())
-        return;
-    for (int k = 1; k < a.levels; ++k) {
-        const u32* jp = a.jump + (size_t)(k - 1) * n;
-        const u64* mp = a.mxo + (size_t)(k - 1) * n;
-        u32* jc = a.jump + (size_t)k * n;
-        u64* mc = a.mxo + (size_t)k * n;
-        for (u32 v = me; v < n; v += ts) {
-            u32 j = jp[v];
-            jc[v] = jp[j];
-            u64 x = mp[v], y = mp[j];
-            mc[v] = x > y ? x : y;
-        }
-        if (!t.sync())
-            return;
-    }
-    // ---- nearest heavier ancestor, and the sort keys (nha, ord)
-    for (u32 y = me + 1; y < n; y += ts) {
-        u32 z = a.parent[y];
-        const u64 tg = a.ord[y];
-        for (int k = a.levels - 1; k >= 0; --k) {
-            if (a.mxo[(size_t)k * n + z] < tg)
-                z = a.jump[(size_t)k * n + z];
-        }
-        a.nha[y] = z;
-        a.skey0[y - 1] = ((u64)z << 48) | tg;
-    }
-    if (!t.sync())
-        return;
-    // ---- stable LSD radix sort of the keys on bits 16..63 (the input is in
-    // increasing y, which is the lowest field)
-    {
-        u64* in = a.skey0;
-        u64* out = a.skey1;
-        const u32 ntiles = a.ntiles;
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        for (int pass = 0; pass < 6; ++pass) {
-            const int shift = 16 + 8 * pass;
-            for (u32 tile = t.block(); tile < ntiles; tile += t.nblocks()) {
-                for (u32 d = threadIdx.x; d < 256; d += blockDim.x)
-                    s_cnt[d] = 0;
-                __syncthreads();
-                const u32 b0 = tile * SORT_TILE, b1 = min(m, b0 + SORT_TILE);
-                for (u32 i = b0 + threadIdx.x; i < b1; i += blockDim.x)
-                    atomicAdd(&s_cnt[(u32)(in[i] >> shift) & 255u], 1u);
-                __syncthreads();
-                for (u32 d = threadIdx.x; d < 256; d += blockDim.x)
-                    a.hist[d * ntiles + tile] = s_cnt[d];
-                __syncthreads();
-            }
-            if (!t.sync())
-                return;
-            u32 htot = 0;
-            if (!team_excl_scan(t, a.hist, a.hist, 256 * ntiles, a.part, &htot))
-                return;
-            if (!t.sync())
-                return;
-            for (u32 tile = t.block(); tile < ntiles; tile += t.nblocks()) {
-                for (u32 d = threadIdx.x; d < 256; d += blockDim.x) {
-                    s_off[d] = a.hist[d * ntiles + tile];
-                    s_cnt[d] = 0;   // running count of this tile
-                }
-                const u32 b0 = tile * SORT_TILE, b1 = min(m, b0 + SORT_TILE);
-                for (u32 base = b0; base < b1; base += blockDim.x) {
-                    const u32 i = base + threadIdx.x;
-                    const bool valid = i < b1;
-                    const u64 key = valid ? in[i] : 0ull;
-                    const u32 d = valid ? ((u32)(key >> shift) & 255u) : (256u + lane);
-                    const u32 peers = __match_any_sync(0xFFFFFFFFu, d);
-                    const u32 rank_w = __popc(peers & ((1u << lane) - 1u));
-                    for (u32 x = threadIdx.x; x < SORT_NW * 256; x += blockDim.x)
-                        (&s_wc[0][0])[x] = 0;
-                    __syncthreads();
-                    if (valid && rank_w == 0)
-                        s_wc[w][d] = __popc(peers);
-                    __syncthreads();
-                    for (u32 dd = threadIdx.x; dd < 256; dd += blockDim.x) {
-                        u32 run = s_cnt[dd];
-                        for (int ww = 0; ww < SORT_NW; ++ww) {
-                            u32 c = s_wc[ww][dd];
-                            s_wc[ww][dd] = run;
-                            run += c;
-                        }
-                        s_cnt[dd] = run;
-                    }
-                    __syncthreads();
-                    if (valid)
-                        out[s_off[d] + s_wc[w][d] + rank_w] = key;
-                    __syncthreads();
-                }
-            }
-            if (!t.sync())
-                return;
-            u64* tmp = in;
-            in = out;
-            out = tmp;
-        }
-        // 6 passes: the sorted keys are back in skey0
-    }
-    // ---- first child / next sibling of the nearest-heavier-ancestor tree
-    for (u32 i = me; i < m; i += ts) {
-        u64 s = a.skey0[i];
-        u32 p = (u32)(s >> 48), y = (u32)s & 0xFFFFu;
-        if (i == 0 || (u32)(a.skey0[i - 1] >> 48) != p)
-            a.first_child[p] = y;
-        a.next_sib[y] = (i + 1 < m && (u32)(a.skey0[i + 1] >> 48) == p)
-                            ? ((u32)a.skey0[i + 1] & 0xFFFFu)
-                            : NONE32;
-    }
-    if (!t.sync())
-        return;
-    // ---- preorder by an Euler tour of that tree: arc 2v goes down into v,
-    // 2v+1 comes back up; down arcs weigh 1
-    for (u32 x = me; x < 2 * n; x += ts) {
-        u32 v = x >> 1, nx, wgt;
-        if (v == 0) {
-            nx = LR_END;
-            wgt = 0;
-        } else if ((x & 1) == 0) {
-            u32 fc = a.first_child[v];
-            nx = fc != NONE32 ? 2 * fc : 2 * v + 1;
-            wgt = 1;
-        } else {
-            u32 ns = a.next_sib[v];
-            u32 p = a.nha[v];
-            nx = ns != NONE32 ? 2 * ns : (p == 0 ? LR_END : 2 * p + 1);
-            wgt = 0;
-        }
-        a.lr_nx0[x] = nx;
-        a.lr_d0[x] = wgt;
-    }
-    if (!t.sync())
-        return;
-    rounds = ceil_log2_dev(2 * n) + 1;
-    which = list_rank(t, 2 * n, a.lr_d0, a.lr_d1, a.lr_nx0, a.lr_nx1, rounds, &ok);
-    if (!ok)
-        return;
-    const u32* suf = which ? a.lr_d1 : a.lr_d0;   // down arcs from here to the end
-    for (u32 v = me; v < n; v += ts) {
-        if (v == 0) {
-            a.pos[0] = 0;
-            a.order[0] = 0;
-            a.nsize[0] = n;
-        } else {
-            u32 sd = suf[2 * v];
-            if (sd < 1 || sd > n - 1) {   // not a tree: report, never write out of range
-                atomicOr(a.status, DEV_INTERNAL);
-                continue;
-            }
-            u32 p = n - sd;
-            a.pos[v] = p;
-            a.order[p] = v;
-            a.gap[p - 1] = a.pe_key[v];
-            a.nsize[v] = sd - suf[2 * v + 1];
-        }
-    }
-    if (!t.sync())
-        return;
-    // ---- sparse table over gap[0..m)
-    for (u32 x = me; x < m; x += ts)
-        a.st[x] = a.gap[x];
-    if (!t.sync())
-        return;
-    for (int k = 1; k < a.st_levels; ++k) {
-        const u32* sp = a.st + (size_t)(k - 1) * n;
-        u32* sc = a.st + (size_t)k * n;
-        const u32 half = 1u << (k - 1);
-        for (u32 x = me; x + 2 * half <= m; x += ts) {
-            u32 p = sp[x], q = sp[x + half];
-            sc[x] = p > q ? p : q;
-        }
-        if (!t.sync())
-            return;
-    }
+    leaf_body(t, a);
 }
 
 cudaError_t run_leaf_order(Workspace& ws, u32* status, cudaStream_t s)

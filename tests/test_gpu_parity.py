@@ -182,3 +182,53 @@ def test_unaligned_pointers(n, shift):
     torch.cuda.synchronize()
     assert appd.last_device_status() == 0
     assert_bits(Mv.cpu().numpy(), ref, f"unaligned n={n} shift={shift}")
+
+
+def _batch(sizes, dtypes, seed0=0):
+    Ws = []
+    for g, (n, dt) in enumerate(zip(sizes, dtypes)):
+        if dt == 1:
+            Ws.append(synth.hash_u32(n, seed=seed0 + g) if n > 0 else np.zeros((0, 0), np.uint32))
+        else:
+            Ws.append(synth.uniform01(n, seed=seed0 + g) if n > 0 else np.zeros((0, 0), np.float32))
+    offs = np.cumsum([0] + [n * n for n in sizes])[:-1].astype(np.int64)
+    flat = np.concatenate([W.view(np.uint32).ravel() for W in Ws] + [np.zeros(1, np.uint32)])
+    return Ws, offs, flat
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+def test_batched_mixed_dtypes_and_cutover(inplace):
+    # sizes on both sides of the cut-over (one CTA per graph up to n_split,
+    # the single-solve pipeline above it), dtypes mixed, empty and 1-vertex graphs
+    sizes = [0, 1, 2, 3, 37, 64, 300, 2048, 2049, 999, 5, 4100]
+    dts = [0, 1, 0, 1, 0, 1, 1, 0, 1, 0, 0, 1]
+    Ws, offs, flat = _batch(sizes, dts, seed0=77)
+    T = torch.from_numpy(flat.view(np.int32)).cuda()
+    out = T if inplace else torch.empty_like(T)
+    appd.solve_batched(T, offs, sizes, dts=dts, out=out)
+    torch.cuda.synchronize()
+    assert appd.last_device_status() == 0
+    Mh = out.cpu().numpy().view(np.uint32)
+    for g, (W, n) in enumerate(zip(Ws, sizes)):
+        if n == 0:
+            continue
+        got = Mh[offs[g]: offs[g] + n * n].reshape(n, n).view(W.dtype)
+        assert_bits(got, oracle.appd(W), f"batched graph {g} n={n} inplace={inplace}")
+
+
+def test_batched_repeat_replays_and_tuning():
+    sizes = [int(x) for x in synth.cfg4_sizes(200)]
+    Ws, offs, flat = _batch(sizes, [0] * len(sizes), seed0=1000)
+    T = torch.from_numpy(flat.view(np.int32)).cuda()
+    refs = [oracle.appd(W) for W in Ws[:25]]
+    for tuning in [(1, 256, 2048), (1, 128, 512), (1, 64, 2048), (1, 512, 100)]:
+        appd.batched_tuning(*tuning)
+        for _ in range(2):   # second call replays the captured launch
+            M = appd.solve_batched(T, offs, sizes)
+            torch.cuda.synchronize()
+            Mh = M.cpu().numpy().view(np.uint32)
+            for g in range(25):
+                n = sizes[g]
+                got = Mh[offs[g]: offs[g] + n * n].reshape(n, n).view(np.float32)
+                assert_bits(got, refs[g], f"graph {g} tuning {tuning}")
+    appd.batched_tuning()
