@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
     return p.parse_args()
 
 
@@ -236,6 +237,102 @@ def bench_batched(steps: int, warmup: int, dev):
             "bytes_w_plus_m": 8.0 * ent}
 
 
+def serving_requests(count: int, seed: int = 5):
+    """n = floor(64 * 128^u) (log-uniform in [64, 8192]), dtype Bernoulli(1/2)."""
+    rng = np.random.default_rng(seed)
+    u = rng.random(count)
+    ns = np.clip(np.floor(64.0 * np.power(128.0, u)).astype(np.int64), 64, 8192)
+    dts = (rng.random(count) < 0.5).astype(np.int64)   # 1 = uint32, 0 = FP32 mixture
+    return ns, dts
+
+
+def run_serving(sv, ns, dts, arrivals, dev, seed: int = 5):
+    """Drives the server: requests arrive at `arrivals` (s, relative); each is
+    admitted when the budget allows, its W generated into the slot on the
+    device, then committed; completions are polled and released.  Returns
+    per-request latency (arrival -> completion seen), ingress times, wall."""
+    import collections
+
+    import torch
+
+    import synth
+    from paper_2407_07058_gb300 import appd
+    N = len(ns)
+    st = torch.cuda.current_stream()
+    lat = np.zeros(N)
+    ingress = []
+    waiting = collections.deque()
+    owner = {}
+    i = done = 0
+    t0 = time.perf_counter()
+    while done < N:
+        now = time.perf_counter() - t0
+        while i < N and arrivals[i] <= now:
+            waiting.append(i)
+            i += 1
+        progressed = False
+        while waiting:
+            k = waiting[0]
+            n, dt = int(ns[k]), int(dts[k])
+            r = sv.submit(n, appd.U32 if dt else appd.F32)
+            if r is None:
+                break
+            waiting.popleft()
+            rid, slot = r
+            tg = time.perf_counter()
+            if dt:
+                synth.device_hash_u32(seed * 1000003 + k, n, slot, st.cuda_stream)
+            else:
+                pts = torch.from_numpy(synth.gmm_points(n, 2, 5, sigma=0.5, seed=seed * 1000003 + k,
+                                                        mean_box=10.0)).to(dev, non_blocking=False)
+                synth.device_euclid(pts.data_ptr(), n, 2, slot, st.cuda_stream)
+            st.synchronize()
+            ingress.append(time.perf_counter() - tg)
+            sv.commit(rid)
+            owner[rid] = k
+            progressed = True
+        for rid, _ in sv.poll(4096):
+            k = owner.pop(rid)
+            lat[k] = time.perf_counter() - t0 - arrivals[k]
+            sv.release(rid)
+            done += 1
+            progressed = True
+        if not progressed:
+            time.sleep(0.0001)
+    return lat, np.array(ingress), time.perf_counter() - t0
+
+
+def bench_serving(dev, count: int = 20000):
+    """Continuous batching under a 40 GB budget: capacity at saturation, then
+    Poisson arrivals at 0.5x and 0.8x of it; graphs/s and p50/p99 latency."""
+    from paper_2407_07058_gb300 import appd
+    budget = 40 << 30
+    ns, dts = serving_requests(count)
+    sv = appd.Server(budget, 8192)
+    try:
+        # warm-up, then capacity: a saturating burst (all arrive at t = 0)
+        run_serving(sv, ns[:200], dts[:200], np.zeros(200), dev)
+        m = min(count, 4000)
+        _, _, wall = run_serving(sv, ns[:m], dts[:m], np.zeros(m), dev)
+        cap = m / wall
+        out = {"workload": f"{count} requests, n log-uniform in [64, 8192], half FP32 2-D "
+                           "mixture distances, half uint32 uniform [0, 2^16); 40 GB budget",
+               "capacity_graphs_per_s": cap, "rates": []}
+        rng = np.random.default_rng(55)
+        for frac in (0.5, 0.8):
+            lam = frac * cap
+            arr = np.cumsum(rng.exponential(1.0 / lam, size=count))
+            lat, ing, wall = run_serving(sv, ns, dts, arr, dev)
+            out["rates"].append({"rate_frac_of_capacity": frac, "rate_per_s": lam,
+                                 "graphs_per_s": count / wall,
+                                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                                 "ingress_p50_ms": 1e3 * float(np.percentile(ing, 50))})
+    finally:
+        sv.close()
+    return out
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args, rank, world):
     if rank != 0:
@@ -377,6 +474,10 @@ def run_ours(args, rank, world, local):
         del W, M
         torch.cuda.empty_cache()
         batched = bench_batched(max(3, min(args.steps, 10)), args.warmup, dev)
+    serving = None
+    if not args.no_serving:
+        torch.cuda.empty_cache()
+        serving = bench_serving(dev)
 
     if rank == 0:
         line = {
@@ -395,6 +496,7 @@ def run_ours(args, rank, world, local):
             "c1": c1,
             "hbm_frac_solve_design_bytes": solve_frac,
             "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -170,6 +170,17 @@ appd_status appd_check_symmetric(const void *W, int64_t n, appd_dtype dt, appd_s
  */
 appd_status appd_last_device_status(appd_stream_t s);
 
+/*
+ * appd_probe_bounded_wait -- failure-detection probe (no counterpart in the
+ * paper).  Launches a two-CTA cooperative kernel in which one CTA never
+ * reaches the grid barrier, so the other CTA's bounded wait runs out after
+ * limit_ms (1..10000) milliseconds and records APPD_ERR_TIMEOUT in the device
+ * status word; both CTAs then return and the context stays usable.  Nothing
+ * faults or hangs.  Returns APPD_OK once enqueued; appd_last_device_status
+ * then reports and clears the timeout.
+ */
+appd_status appd_probe_bounded_wait(int32_t limit_ms, appd_stream_t s);
+
 /* Frees every cached workspace on the current device (synchronizes it). */
 appd_status appd_release_workspaces(void);
 

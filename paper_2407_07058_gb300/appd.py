@@ -24,7 +24,8 @@ STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD
 # every symbol that include/appd.h declares
 EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host", "appd_mst",
            "appd_leaf_order", "appd_solve_batched", "appd_batched_tuning", "appd_check_symmetric",
-           "appd_last_device_status", "appd_release_workspaces", "appd_profile_begin",
+           "appd_last_device_status", "appd_probe_bounded_wait", "appd_release_workspaces",
+           "appd_profile_begin",
            "appd_profile_end", "appd_server_create",
            "appd_server_submit", "appd_server_commit", "appd_server_poll", "appd_server_release",
            "appd_server_destroy"]
@@ -60,6 +61,7 @@ def load(build_if_missing: bool = True):
             "appd_batched_tuning": [i32, i32, i64],
             "appd_check_symmetric": [vp, i64, ci, vp],
             "appd_last_device_status": [vp],
+            "appd_probe_bounded_wait": [i32, vp],
             "appd_release_workspaces": [],
             "appd_server_create": [ctypes.c_size_t, i32, ctypes.POINTER(vp)],
             "appd_server_submit": [vp, i64, ci, ctypes.POINTER(u64), ctypes.POINTER(vp)],
@@ -221,8 +223,27 @@ def batched_tuning(ctas_per_sm: int = 1, fill_rows: int = 256, n_split: int = 20
     _check(load().appd_batched_tuning(ctas_per_sm, fill_rows, n_split), "appd_batched_tuning")
 
 
+def probe_bounded_wait(limit_ms: int = 200, stream=None):
+    """Run a grid-barrier wait out on purpose (bounded; see appd.h)."""
+    _check(load().appd_probe_bounded_wait(limit_ms, _stream_ptr(stream)), "appd_probe_bounded_wait")
+
+
 def release_workspaces():
     _check(load().appd_release_workspaces(), "appd_release_workspaces")
+
+
+class _DevPtr:
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n, n), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def device_view(ptr: int, n: int, dt: int):
+    """A torch tensor viewing an n x n matrix at a raw device pointer (e.g. a
+    server slot); float32 for F32, int32 for U32.  No copy."""
+    import torch
+    return torch.as_tensor(_DevPtr(ptr, n, "<f4" if dt == F32 else "<i4"), device="cuda")
 
 
 class Server:

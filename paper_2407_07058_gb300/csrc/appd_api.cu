@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -18,6 +19,8 @@ std::mutex g_mu;
 Workspace* g_ws[MAX_DEV] = {};
 u32* g_status[MAX_DEV] = {};
 BatchTuning g_tune;
+BatchRuntime* g_brt[MAX_DEV] = {};
+BatchTuning g_brt_tune[MAX_DEV];
 
 // ------------------------------------------------------------- profiling
 struct ProfMark {
@@ -95,9 +98,55 @@ size_t appd::workspace_layout(Workspace& w, char* base, int64_t cap)
     return align_up(off, 256);
 }
 
-namespace {
+cudaError_t appd::workspace_create(int64_t n, Workspace** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    int64_t cap = 1024;
+    while (cap < n)
+        cap *= 2;
+    if (cap > 65536)
+        cap = 65536;
+    Workspace* nw = new Workspace();
+    nw->device = dev;
+    nw->cap = cap;
+    nw->n = 0;
+    const size_t bytes = workspace_layout(*nw, nullptr, cap);
+    void* base = nullptr;
+    e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) {
+        delete nw;
+        return e;
+    }
+    workspace_layout(*nw, (char*)base, cap);
+    nw->base = base;
+    nw->bytes = bytes;
+    cudaDeviceGetAttribute(&nw->sms, cudaDevAttrMultiProcessorCount, dev);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    nw->coop_blocks = nw->sms;
+    nw->coop_threads = 512;
+    nw->contract_blocks = nw->sms;
+    nw->bin_cap = (u32)((smem_optin - 2048) / 8);
+    *out = nw;
+    return cudaSuccess;
+}
 
-size_t carve(Workspace& w, char* base, int64_t cap) { return workspace_layout(w, base, cap); }
+void appd::workspace_destroy(Workspace* w)
+{
+    if (!w)
+        return;
+    cudaDeviceSynchronize();
+    cudaFree(w->base);
+    cudaFree(w->cscratch);
+    cudaFree(w->hostW);
+    cudaFree(w->hostM);
+    delete w;
+}
+
+namespace {
 
 // The device's workspace with capacity >= n (grown if needed).
 appd_status get_ws(int64_t n, Workspace** out)
@@ -111,42 +160,13 @@ appd_status get_ws(int64_t n, Workspace** out)
         *out = w;
         return APPD_OK;
     }
-    int64_t cap = 1024;
-    while (cap < n)
-        cap *= 2;
-    if (cap > 65536)
-        cap = 65536;
-    Workspace* nw = new Workspace();
-    nw->device = dev;
-    nw->cap = cap;
-    nw->n = 0;
-    size_t bytes = carve(*nw, nullptr, cap);
-    void* base = nullptr;
     if (w) {
-        cudaDeviceSynchronize();
-        cudaFree(w->base);
-        cudaFree(w->cscratch);
-        cudaFree(w->hostW);
-        cudaFree(w->hostM);
-        delete w;
+        workspace_destroy(w);
         w = nullptr;
     }
-    e = cudaMalloc(&base, bytes);
-    if (e != cudaSuccess) {
-        delete nw;
+    e = workspace_create(n, &w);
+    if (e != cudaSuccess)
         return cuda_fail(e);
-    }
-    carve(*nw, (char*)base, cap);
-    nw->base = base;
-    nw->bytes = bytes;
-    cudaDeviceGetAttribute(&nw->sms, cudaDevAttrMultiProcessorCount, dev);
-    int smem_optin = 0;
-    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    nw->coop_blocks = nw->sms;
-    nw->coop_threads = 512;
-    nw->contract_blocks = nw->sms;
-    nw->bin_cap = (u32)((smem_optin - 2048) / 8);
-    w = nw;
     *out = w;
     return APPD_OK;
 }
@@ -254,16 +274,14 @@ appd_status ensure_cscratch(Workspace& w, int64_t n)
     return APPD_OK;
 }
 
-appd_status solve_impl(const void* W, int64_t n, int dt, void* M, cudaStream_t s, bool alg4)
+appd_status solve_with(Workspace& w, u32* status, const void* W, int64_t n, int dt, void* M,
+                       cudaStream_t s, bool alg4)
 {
-    appd_status st = check_args(W, n, dt, M);
-    if (st != APPD_OK || n == 0)
-        return st;
-    std::lock_guard<std::mutex> lk(g_mu);
     SolveCtx c;
-    if ((st = prepare(n, c)) != APPD_OK)
-        return st;
-    Workspace& w = *c.ws;
+    c.ws = &w;
+    c.status = status;
+    c.cap = w.cap;
+    appd_status st;
     void* cbuf = M;
     if (M == W) {
         if ((st = ensure_cscratch(w, n)) != APPD_OK)
@@ -278,6 +296,27 @@ appd_status solve_impl(const void* W, int64_t n, int dt, void* M, cudaStream_t s
     prof_end(PH_FILL, s);
     prof_launches(alg4 ? 4 : 1);
     return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
+appd_status solve_impl(const void* W, int64_t n, int dt, void* M, cudaStream_t s, bool alg4)
+{
+    appd_status st = check_args(W, n, dt, M);
+    if (st != APPD_OK || n == 0)
+        return st;
+    std::lock_guard<std::mutex> lk(g_mu);
+    SolveCtx c;
+    if ((st = prepare(n, c)) != APPD_OK)
+        return st;
+    return solve_with(*c.ws, c.status, W, n, dt, M, s, alg4);
+}
+
+// Probe of the bounded grid barrier: CTA 1 never arrives, so CTA 0's wait
+// runs out after limit_ns and records DEV_TIMEOUT; both CTAs then return.
+__global__ void k_wait_probe(GridBar* bar, u32* status, u64 limit_ns)
+{
+    if (blockIdx.x != 0)
+        return;
+    grid_sync(bar, status, limit_ns);
 }
 
 __global__ void k_check_sym(const u32* __restrict__ W, u32 n, u32* __restrict__ bad)
@@ -327,6 +366,21 @@ void prof_launches(int k)
 }
 
 }  // namespace appd
+
+int appd::solve_on(Workspace& ws, u32* status, const void* W, int64_t n, int dt, void* M,
+                   cudaStream_t s, bool alg4)
+{
+    if (n == 0)
+        return APPD_OK;
+    return (int)solve_with(ws, status, W, n, dt, M, s, alg4);
+}
+
+u32* appd::device_status_word()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    u32* st = nullptr;
+    return get_status(&st) == APPD_OK ? st : nullptr;
+}
 
 extern "C" {
 
@@ -516,30 +570,45 @@ appd_status appd_solve_batched(const int64_t* offsets, const void* Ws, const int
         std::lock_guard<std::mutex> lk(g_mu);
         tune = g_tune;
     }
-    std::vector<int32_t> small;
+    BatchDesc d;
     for (int32_t g = 0; g < count; ++g) {
         if (ns[g] == 0)
             continue;
+        const u32* W = (const u32*)Ws + offsets[g];
+        u32* M = (u32*)Ms + offsets[g];
+        const uint8_t dt = dts ? dts[g] : (uint8_t)APPD_F32;
         if (ns[g] <= tune.n_split) {
-            small.push_back(g);
+            d.w.push_back(W);
+            d.m.push_back(M);
+            d.n.push_back((u32)ns[g]);
+            d.dt.push_back(dt);
         } else {
-            const u32* W = (const u32*)Ws + offsets[g];
-            u32* M = (u32*)Ms + offsets[g];
-            appd_status st = appd_solve(W, ns[g], dts ? (appd_dtype)dts[g] : APPD_F32, M, s);
+            appd_status st = appd_solve(W, ns[g], (appd_dtype)dt, M, s);
             if (st != APPD_OK)
                 return st;
         }
     }
-    if (small.empty())
+    if (d.n.empty())
         return APPD_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
     u32* status = nullptr;
     appd_status st;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if ((st = get_status(&status)) != APPD_OK)
-            return st;
+    if ((st = get_status(&status)) != APPD_OK)
+        return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return APPD_ERR_CUDA;
+    const int64_t nmax = *std::max_element(d.n.begin(), d.n.end());
+    BatchRuntime*& rt = g_brt[dev];
+    if (!rt || batch_runtime_cap(rt) < nmax || !(g_brt_tune[dev] == tune)) {
+        batch_runtime_destroy(rt);
+        rt = nullptr;
+        cudaError_t e = batch_runtime_create(nmax, tune, &rt);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        g_brt_tune[dev] = tune;
     }
-    cudaError_t e = run_batched(offsets, Ws, ns, dts, Ms, small, tune, status, (cudaStream_t)s);
+    cudaError_t e = batch_launch(*rt, d, status, (cudaStream_t)s, true);
     return e == cudaSuccess ? APPD_OK : cuda_fail(e);
 }
 
@@ -586,6 +655,29 @@ appd_status appd_check_symmetric(const void* W, int64_t n, appd_dtype dt, appd_s
     return h ? APPD_ERR_ASYMMETRIC : APPD_OK;
 }
 
+appd_status appd_probe_bounded_wait(int32_t limit_ms, appd_stream_t s)
+{
+    if (limit_ms < 1 || limit_ms > 10000)
+        return APPD_ERR_INVALID;
+    u32* status = nullptr;
+    appd_status st;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if ((st = get_status(&status)) != APPD_OK)
+            return st;
+    }
+    cudaStream_t cs = (cudaStream_t)s;
+    GridBar* bar = reinterpret_cast<GridBar*>(status + 32);   // scratch words of the status block
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), cs);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    void* args[] = {&bar, &status, nullptr};
+    u64 lim = (u64)limit_ms * 1000000ull;
+    args[2] = &lim;
+    e = cudaLaunchCooperativeKernel((const void*)k_wait_probe, dim3(2), dim3(32), args, 0, cs);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
 appd_status appd_last_device_status(appd_stream_t s)
 {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)s);
@@ -622,14 +714,11 @@ appd_status appd_release_workspaces(void)
         return APPD_ERR_CUDA;
     cudaDeviceSynchronize();
     if (g_ws[dev]) {
-        cudaFree(g_ws[dev]->base);
-        cudaFree(g_ws[dev]->cscratch);
-        cudaFree(g_ws[dev]->hostW);
-        cudaFree(g_ws[dev]->hostM);
-        delete g_ws[dev];
+        workspace_destroy(g_ws[dev]);
         g_ws[dev] = nullptr;
     }
-    release_batched_runtime();
+    batch_runtime_destroy(g_brt[dev]);
+    g_brt[dev] = nullptr;
     return APPD_OK;
 }
 

@@ -42,14 +42,13 @@ struct SliceWs {
 };
 
 struct BatchArgs {
-    const int64_t* offsets;
-    const int64_t* ns;
-    const uint8_t* dts;   // may be null: all FP32
-    const u32* queue;     // graph indices, largest first
+    const u32* const* wp;   // per-graph W (device pointers)
+    u32* const* mp;         // per-graph M
+    const u32* ns;          // per-graph n
+    const uint8_t* dts;     // per-graph dtype
+    const u32* queue;       // graph indices, largest first
     u32 count;
-    const u32* Ws;
-    u32* Ms;
-    u32* next;            // work-queue head
+    u32* next;              // work-queue head
     SliceWs* slices;
     u32* status;
     u32 bin_cap;          // u64 bins that fit the dynamic shared memory
@@ -241,12 +240,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
         if (q >= b.count)
             break;
         const u32 g = b.queue[q];
-        const u32 n = (u32)b.ns[g];
-        const u32* W = b.Ws + b.offsets[g];
-        u32* M = b.Ms + b.offsets[g];
+        const u32 n = b.ns[g];
+        const u32* W = b.wp[g];
+        u32* M = b.mp[g];
         if (n == 0)
             continue;
-        if (b.dts && b.dts[g] == 1)
+        if (b.dts[g] == 1)
             solve_one<1>(w, W, M, n, b, smem, s_rows, s_red);
         else
             solve_one<0>(w, W, M, n, b, smem, s_rows, s_red);
@@ -254,35 +253,28 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
 }
 
 // ------------------------------------------------------------------ host
-namespace {
-
-// per-device batch runtime: workspace slices and cached launch plans
 struct BatchRuntime {
     int device = -1;
     int sms = 0;
     int nslices = 0;
     int64_t cap = 0;
+    BatchTuning tune;
     void* slice_mem = nullptr;
     SliceWs* d_slices = nullptr;
     void* scratch_mem = nullptr;   // per-slice contraction scratch for in-place graphs
-    size_t scratch_per_slice = 0;
     u32* d_next = nullptr;
+    void* d_desc = nullptr;        // descriptors of the uncached launch path
+    size_t desc_bytes = 0;
     size_t smem = 0;
     u32 bin_cap = 0;
-    u32 fill_rows = 0;
     struct Plan {
-        void* dev = nullptr;   // offsets | ns | dts | queue
+        void* dev = nullptr;
         cudaGraphExec_t exec = nullptr;
-        cudaStream_t stream = nullptr;
-        u32 count = 0;
     };
     std::map<std::vector<int64_t>, Plan> plans;
 };
 
-std::mutex g_bmu;
-BatchRuntime* g_brt[64] = {};
-
-size_t slice_bytes(int64_t cap, Workspace& tmp) { return workspace_layout(tmp, nullptr, cap); }
+namespace {
 
 SliceWs to_slice(const Workspace& w)
 {
@@ -334,43 +326,83 @@ SliceWs to_slice(const Workspace& w)
     return s;
 }
 
-cudaError_t get_runtime(int64_t cap, const BatchTuning& tune, BatchRuntime** out)
+cudaError_t ensure_scratch(BatchRuntime& rt)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    if (rt.scratch_mem)
+        return cudaSuccess;
+    const size_t per = (contraction_scratch_bytes(rt.cap) + 255) & ~(size_t)255;
+    cudaError_t e = cudaMalloc(&rt.scratch_mem, per * rt.nslices);
     if (e != cudaSuccess)
         return e;
-    BatchRuntime*& rt = g_brt[dev];
-    const int want_slices_per_sm = tune.ctas_per_sm;
-    if (rt && rt->cap >= cap && rt->fill_rows == (u32)tune.fill_rows &&
-        rt->nslices == rt->sms * want_slices_per_sm) {
-        *out = rt;
-        return cudaSuccess;
-    }
-    if (rt) {
-        cudaDeviceSynchronize();
-        for (auto& kv : rt->plans) {
-            cudaGraphExecDestroy(kv.second.exec);
-            cudaFree(kv.second.dev);
-        }
-        cudaFree(rt->slice_mem);
-        cudaFree(rt->d_slices);
-        cudaFree(rt->scratch_mem);
-        cudaFree(rt->d_next);
-        delete rt;
-        rt = nullptr;
-    }
+    std::vector<SliceWs> hs(rt.nslices);
+    e = cudaMemcpy(hs.data(), rt.d_slices, sizeof(SliceWs) * rt.nslices, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return e;
+    for (int i = 0; i < rt.nslices; ++i)
+        hs[i].cscratch = (u64*)((char*)rt.scratch_mem + per * i);
+    return cudaMemcpy(rt.d_slices, hs.data(), sizeof(SliceWs) * rt.nslices, cudaMemcpyHostToDevice);
+}
+
+// descriptor block layout: wp | mp | ns | queue | dts
+size_t desc_layout(u32 cnt, size_t off[5])
+{
+    off[0] = 0;
+    off[1] = off[0] + 8 * (size_t)cnt;
+    off[2] = off[1] + 8 * (size_t)cnt;
+    off[3] = off[2] + 4 * (size_t)cnt;
+    off[4] = off[3] + 4 * (size_t)cnt;
+    return (off[4] + cnt + 255) & ~(size_t)255;
+}
+
+void fill_desc(const BatchDesc& d, std::vector<unsigned char>& host, const size_t off[5])
+{
+    const u32 cnt = (u32)d.n.size();
+    std::vector<u32> q(cnt);
+    std::iota(q.begin(), q.end(), 0u);
+    std::stable_sort(q.begin(), q.end(), [&](u32 a, u32 b) { return d.n[a] > d.n[b]; });
+    memcpy(host.data() + off[0], d.w.data(), 8 * cnt);
+    memcpy(host.data() + off[1], d.m.data(), 8 * cnt);
+    memcpy(host.data() + off[2], d.n.data(), 4 * cnt);
+    memcpy(host.data() + off[3], q.data(), 4 * cnt);
+    memcpy(host.data() + off[4], d.dt.data(), cnt);
+}
+
+BatchArgs make_args(const BatchRuntime& rt, void* dev, const size_t off[5], u32 cnt, u32* status)
+{
+    BatchArgs a;
+    a.wp = (const u32* const*)((char*)dev + off[0]);
+    a.mp = (u32* const*)((char*)dev + off[1]);
+    a.ns = (const u32*)((char*)dev + off[2]);
+    a.queue = (const u32*)((char*)dev + off[3]);
+    a.dts = (const uint8_t*)((char*)dev + off[4]);
+    a.count = cnt;
+    a.next = rt.d_next;
+    a.slices = rt.d_slices;
+    a.status = status;
+    a.bin_cap = rt.bin_cap;
+    a.fill_rows = (u32)rt.tune.fill_rows;
+    return a;
+}
+
+}  // namespace
+
+cudaError_t batch_runtime_create(int64_t cap, const BatchTuning& tune, BatchRuntime** out)
+{
     BatchRuntime* nr = new BatchRuntime();
-    nr->device = dev;
-    cudaDeviceGetAttribute(&nr->sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaGetDevice(&nr->device);
+    if (e != cudaSuccess) {
+        delete nr;
+        return e;
+    }
+    cudaDeviceGetAttribute(&nr->sms, cudaDevAttrMultiProcessorCount, nr->device);
     int64_t c = 1024;
     while (c < cap)
         c *= 2;
     nr->cap = c;
-    nr->nslices = nr->sms * want_slices_per_sm;
-    nr->fill_rows = (u32)tune.fill_rows;
+    nr->tune = tune;
+    nr->nslices = nr->sms * tune.ctas_per_sm;
     Workspace tmp;
-    const size_t per = (slice_bytes(c, tmp) + 255) & ~(size_t)255;
+    const size_t per = (workspace_layout(tmp, nullptr, c) + 255) & ~(size_t)255;
     if ((e = cudaMalloc(&nr->slice_mem, per * nr->nslices)) != cudaSuccess) {
         delete nr;
         return e;
@@ -381,148 +413,27 @@ cudaError_t get_runtime(int64_t cap, const BatchTuning& tune, BatchRuntime** out
         workspace_layout(w, (char*)nr->slice_mem + per * i, c);
         hs[i] = to_slice(w);
     }
-    if ((e = cudaMalloc(&nr->d_slices, sizeof(SliceWs) * nr->nslices)) != cudaSuccess)
-        return e;
-    if ((e = cudaMemcpy(nr->d_slices, hs.data(), sizeof(SliceWs) * nr->nslices,
-                        cudaMemcpyHostToDevice)) != cudaSuccess)
-        return e;
-    if ((e = cudaMalloc(&nr->d_next, 256)) != cudaSuccess)
-        return e;
-    // dynamic shared memory: the larger of the fill tile and the bins
-    nr->smem = fill_smem_bytes(nr->fill_rows);
+    if ((e = cudaMalloc(&nr->d_slices, sizeof(SliceWs) * nr->nslices)) == cudaSuccess)
+        e = cudaMemcpy(nr->d_slices, hs.data(), sizeof(SliceWs) * nr->nslices, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&nr->d_next, 256);
+    // dynamic shared memory: the fill tile (the contraction bins fit inside it)
+    nr->smem = fill_smem_bytes((u32)tune.fill_rows);
     nr->bin_cap = (u32)(nr->smem / sizeof(u64));
-    e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nr->smem);
-    if (e != cudaSuccess)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nr->smem);
+    if (e != cudaSuccess) {
+        batch_runtime_destroy(nr);
         return e;
-    rt = nr;
-    *out = rt;
+    }
+    *out = nr;
     return cudaSuccess;
 }
 
-cudaError_t ensure_scratch(BatchRuntime& rt)
+void batch_runtime_destroy(BatchRuntime* rt)
 {
-    if (rt.scratch_mem)
-        return cudaSuccess;
-    const size_t per = (contraction_scratch_bytes(rt.cap) + 255) & ~(size_t)255;
-    cudaError_t e = cudaMalloc(&rt.scratch_mem, per * rt.nslices);
-    if (e != cudaSuccess)
-        return e;
-    rt.scratch_per_slice = per;
-    std::vector<SliceWs> hs(rt.nslices);
-    e = cudaMemcpy(hs.data(), rt.d_slices, sizeof(SliceWs) * rt.nslices, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess)
-        return e;
-    for (int i = 0; i < rt.nslices; ++i)
-        hs[i].cscratch = (u64*)((char*)rt.scratch_mem + per * i);
-    return cudaMemcpy(rt.d_slices, hs.data(), sizeof(SliceWs) * rt.nslices, cudaMemcpyHostToDevice);
-}
-
-}  // namespace
-
-cudaError_t run_batched(const int64_t* offsets, const void* Ws, const int64_t* ns,
-                        const uint8_t* dts, void* Ms, const std::vector<int32_t>& small,
-                        const BatchTuning& tune, u32* status, cudaStream_t s)
-{
-    if (small.empty())
-        return cudaSuccess;
-    std::lock_guard<std::mutex> lk(g_bmu);
-    int64_t nmax = 1;
-    bool inplace = false;
-    for (int32_t g : small) {
-        nmax = std::max<int64_t>(nmax, ns[g]);
-        inplace |= (offsets && Ws == Ms);
-    }
-    BatchRuntime* rt = nullptr;
-    cudaError_t e = get_runtime(nmax, tune, &rt);
-    if (e != cudaSuccess)
-        return e;
-    if (inplace && (e = ensure_scratch(*rt)) != cudaSuccess)
-        return e;
-    // plan key: layout, pointers, stream
-    std::vector<int64_t> key;
-    key.reserve(small.size() * 3 + 4);
-    key.push_back((int64_t)(uintptr_t)Ws);
-    key.push_back((int64_t)(uintptr_t)Ms);
-    key.push_back((int64_t)(uintptr_t)s);
-    for (int32_t g : small) {
-        key.push_back(offsets[g]);
-        key.push_back(ns[g]);
-        key.push_back(dts ? dts[g] : 0);
-    }
-    auto it = rt->plans.find(key);
-    if (it == rt->plans.end()) {
-        // device copies of the descriptors, queue largest first
-        const u32 cnt = (u32)small.size();
-        std::vector<int64_t> hoff(cnt), hn(cnt);
-        std::vector<uint8_t> hdt(cnt);
-        for (u32 i = 0; i < cnt; ++i) {
-            hoff[i] = offsets[small[i]];
-            hn[i] = ns[small[i]];
-            hdt[i] = dts ? dts[small[i]] : 0;
-        }
-        std::vector<u32> q(cnt);
-        std::iota(q.begin(), q.end(), 0u);
-        std::stable_sort(q.begin(), q.end(), [&](u32 a, u32 b) { return hn[a] > hn[b]; });
-        const size_t b_off = 0, b_n = 8 * (size_t)cnt, b_dt = 16 * (size_t)cnt,
-                     b_q = (17 * (size_t)cnt + 15) & ~(size_t)15, total = b_q + 4 * (size_t)cnt;
-        BatchRuntime::Plan p;
-        p.count = cnt;
-        if ((e = cudaMalloc(&p.dev, total)) != cudaSuccess)
-            return e;
-        std::vector<unsigned char> host(total);
-        memcpy(host.data() + b_off, hoff.data(), 8 * cnt);
-        memcpy(host.data() + b_n, hn.data(), 8 * cnt);
-        memcpy(host.data() + b_dt, hdt.data(), cnt);
-        memcpy(host.data() + b_q, q.data(), 4 * cnt);
-        if ((e = cudaMemcpy(p.dev, host.data(), total, cudaMemcpyHostToDevice)) != cudaSuccess)
-            return e;
-        BatchArgs a;
-        a.offsets = (const int64_t*)((char*)p.dev + b_off);
-        a.ns = (const int64_t*)((char*)p.dev + b_n);
-        a.dts = (const uint8_t*)((char*)p.dev + b_dt);
-        a.queue = (const u32*)((char*)p.dev + b_q);
-        a.count = cnt;
-        a.Ws = (const u32*)Ws;
-        a.Ms = (u32*)Ms;
-        a.next = rt->d_next;
-        a.slices = rt->d_slices;
-        a.status = status;
-        a.bin_cap = rt->bin_cap;
-        a.fill_rows = rt->fill_rows;
-        // capture queue reset + persistent kernel into a CUDA graph
-        cudaStream_t cap_s;
-        if ((e = cudaStreamCreateWithFlags(&cap_s, cudaStreamNonBlocking)) != cudaSuccess)
-            return e;
-        cudaGraph_t graph;
-        e = cudaStreamBeginCapture(cap_s, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaMemsetAsync(rt->d_next, 0, sizeof(u32), cap_s);
-            k_batched<<<rt->nslices, BATCH_THREADS, rt->smem, cap_s>>>(a);
-            e = cudaStreamEndCapture(cap_s, &graph);
-        }
-        if (e == cudaSuccess) {
-            e = cudaGraphInstantiate(&p.exec, graph, 0);
-            cudaGraphDestroy(graph);
-        }
-        cudaStreamDestroy(cap_s);
-        if (e != cudaSuccess)
-            return e;
-        it = rt->plans.emplace(key, p).first;
-    }
-    prof_launches(1);
-    prof_begin(PH_BATCHED, s);
-    e = cudaGraphLaunch(it->second.exec, s);
-    prof_end(PH_BATCHED, s);
-    return e;
-}
-
-void release_batched_runtime()
-{
-    std::lock_guard<std::mutex> lk(g_bmu);
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || !g_brt[dev])
+    if (!rt)
         return;
-    BatchRuntime* rt = g_brt[dev];
     cudaDeviceSynchronize();
     for (auto& kv : rt->plans) {
         cudaGraphExecDestroy(kv.second.exec);
@@ -532,8 +443,95 @@ void release_batched_runtime()
     cudaFree(rt->d_slices);
     cudaFree(rt->scratch_mem);
     cudaFree(rt->d_next);
+    cudaFree(rt->d_desc);
     delete rt;
-    g_brt[dev] = nullptr;
+}
+
+int64_t batch_runtime_cap(const BatchRuntime* rt) { return rt->cap; }
+
+cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cudaStream_t s,
+                         bool cache_graph)
+{
+    const u32 cnt = (u32)d.n.size();
+    if (cnt == 0)
+        return cudaSuccess;
+    cudaError_t e;
+    bool inplace = false;
+    for (u32 i = 0; i < cnt; ++i)
+        inplace |= (d.w[i] == (const void*)d.m[i]);
+    if (inplace && (e = ensure_scratch(rt)) != cudaSuccess)
+        return e;
+    size_t off[5];
+    const size_t bytes = desc_layout(cnt, off);
+    std::vector<unsigned char> host(bytes);
+    if (!cache_graph) {
+        // one descriptor block per runtime: launches on the runtime are
+        // ordered on its stream, so the next upload follows the last kernel
+        if (rt.desc_bytes < bytes) {
+            cudaFree(rt.d_desc);
+            rt.d_desc = nullptr;
+            rt.desc_bytes = 0;
+            if ((e = cudaMalloc(&rt.d_desc, bytes)) != cudaSuccess)
+                return e;
+            rt.desc_bytes = bytes;
+        }
+        fill_desc(d, host, off);
+        // pageable source: the copy is staged before the call returns
+        if ((e = cudaMemcpyAsync(rt.d_desc, host.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(rt.d_next, 0, sizeof(u32), s)) != cudaSuccess)
+            return e;
+        BatchArgs a = make_args(rt, rt.d_desc, off, cnt, status);
+        prof_launches(1);
+        prof_begin(PH_BATCHED, s);
+        k_batched<<<rt.nslices, BATCH_THREADS, rt.smem, s>>>(a);
+        prof_end(PH_BATCHED, s);
+        return cudaGetLastError();
+    }
+    std::vector<int64_t> key;
+    key.reserve(4 * cnt + 1);
+    key.push_back((int64_t)(uintptr_t)s);
+    for (u32 i = 0; i < cnt; ++i) {
+        key.push_back((int64_t)(uintptr_t)d.w[i]);
+        key.push_back((int64_t)(uintptr_t)d.m[i]);
+        key.push_back(d.n[i]);
+        key.push_back(d.dt[i]);
+    }
+    auto it = rt.plans.find(key);
+    if (it == rt.plans.end()) {
+        BatchRuntime::Plan p;
+        if ((e = cudaMalloc(&p.dev, bytes)) != cudaSuccess)
+            return e;
+        fill_desc(d, host, off);
+        if ((e = cudaMemcpy(p.dev, host.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        BatchArgs a = make_args(rt, p.dev, off, cnt, status);
+        cudaStream_t cap_s;
+        if ((e = cudaStreamCreateWithFlags(&cap_s, cudaStreamNonBlocking)) != cudaSuccess)
+            return e;
+        cudaGraph_t graph;
+        e = cudaStreamBeginCapture(cap_s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(rt.d_next, 0, sizeof(u32), cap_s);
+            k_batched<<<rt.nslices, BATCH_THREADS, rt.smem, cap_s>>>(a);
+            e = cudaStreamEndCapture(cap_s, &graph);
+        }
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&p.exec, graph, 0);
+            cudaGraphDestroy(graph);
+        }
+        cudaStreamDestroy(cap_s);
+        if (e != cudaSuccess) {
+            cudaFree(p.dev);
+            return e;
+        }
+        it = rt.plans.emplace(key, p).first;
+    }
+    prof_launches(1);
+    prof_begin(PH_BATCHED, s);
+    e = cudaGraphLaunch(it->second.exec, s);
+    prof_end(PH_BATCHED, s);
+    return e;
 }
 
 }  // namespace appd

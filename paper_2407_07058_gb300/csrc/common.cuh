@@ -146,14 +146,17 @@ __device__ __forceinline__ u32 block_excl_scan(u32 v, u32* total, u32* sh)
 // ------------------------------------------------------------ grid barrier
 // Generation barrier for cooperative launches (all CTAs co-resident).  The
 // wait is bounded: after BARRIER_TIMEOUT_NS a CTA records DEV_TIMEOUT and
-// returns false; callers then leave the kernel.  The count word must be zero
-// when the kernel starts (the host clears it before each launch).
+// returns false; callers then leave the kernel.  The count and abort words
+// must be zero when the kernel starts (the host clears them before each
+// launch).
 struct GridBar {
     u32 count;
+    u32 abort;   // set by the first CTA that gave up; later barriers of the launch fail at once
     u32 gen;
 };
 
-__device__ __forceinline__ bool grid_sync(GridBar* bar, u32* status)
+__device__ __forceinline__ bool grid_sync(GridBar* bar, u32* status,
+                                          u64 limit_ns = BARRIER_TIMEOUT_NS)
 {
     __shared__ u32 s_ok;
     __syncthreads();
@@ -161,8 +164,8 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, u32* status)
         s_ok = 1;
     if (threadIdx.x == 0) {
         u32 ok = 1;
-        // once any CTA has given up, every later barrier fails at once
-        if (ld_acquire(status) & DEV_TIMEOUT) {
+        // once any CTA of this launch has given up, every later barrier fails at once
+        if (ld_acquire(&bar->abort)) {
             s_ok = 0;
         }
         u32 g = ld_acquire(&bar->gen);
@@ -176,7 +179,8 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, u32* status)
             u64 t0 = globaltimer_ns();
             while (s_ok && ld_acquire(&bar->gen) == g) {
                 __nanosleep(40);
-                if (globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
+                if (globaltimer_ns() - t0 > limit_ns) {
+                    atomicExch(&bar->abort, 1u);
                     atomicOr(status, DEV_TIMEOUT);
                     ok = 0;
                     break;

@@ -100,11 +100,35 @@ struct BatchTuning {
     int ctas_per_sm = 1;     // persistent CTAs per SM (one workspace slice each)
     int fill_rows = 256;     // rows per fill tile inside a CTA
     int64_t n_split = 2048;  // larger graphs use the single-solve pipeline
+    bool operator==(const BatchTuning& o) const
+    {
+        return ctas_per_sm == o.ctas_per_sm && fill_rows == o.fill_rows && n_split == o.n_split;
+    }
 };
-cudaError_t run_batched(const int64_t* offsets, const void* Ws, const int64_t* ns, const uint8_t* dts,
-                        void* Ms, const std::vector<int32_t>& small, const BatchTuning& tune,
-                        u32* status, cudaStream_t s);
-void release_batched_runtime();
+// host description of one batch of small graphs
+struct BatchDesc {
+    std::vector<const void*> w;
+    std::vector<void*> m;
+    std::vector<u32> n;
+    std::vector<uint8_t> dt;
+};
+struct BatchRuntime;   // workspace slices + cached launch plans (batched.cu)
+cudaError_t batch_runtime_create(int64_t cap, const BatchTuning& tune, BatchRuntime** out);
+void batch_runtime_destroy(BatchRuntime* rt);
+int64_t batch_runtime_cap(const BatchRuntime* rt);
+// Launches one batch on stream s (cache_graph: capture the launch once per
+// layout and replay it; otherwise upload descriptors and launch directly).
+// Launches on one runtime must be ordered (one stream).
+cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cudaStream_t s,
+                         bool cache_graph);
+
+// single solve on an explicit workspace; returns an appd_status code
+int solve_on(Workspace& ws, u32* status, const void* W, int64_t n, int dt, void* M,
+             cudaStream_t s, bool alg4);
+// the current device's status word
+u32* device_status_word();
+cudaError_t workspace_create(int64_t cap, Workspace** out);
+void workspace_destroy(Workspace* w);
 
 // sizes
 size_t contraction_scratch_bytes(int64_t n);

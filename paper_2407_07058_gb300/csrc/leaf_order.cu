@@ -69,7 +69,7 @@ cudaError_t run_leaf_order(Workspace& ws, u32* status, cudaStream_t s)
     a.part = ws.part;
     a.ctr = ws.ctr;
     a.status = status;
-    cudaError_t err = cudaMemsetAsync(&ws.ctr->bar.count, 0, sizeof(u32), s);
+    cudaError_t err = cudaMemsetAsync(&ws.ctr->bar, 0, 2 * sizeof(u32), s);
     if (err != cudaSuccess)
         return err;
     void* args[] = {&a};

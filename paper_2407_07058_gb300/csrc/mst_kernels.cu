@@ -217,6 +217,7 @@ __global__ void k_mst_init(Counters* ctr, u32* comp, u32 n, u32 bar_reset)
         ctr->jump_flag[0] = ctr->jump_flag[1] = ctr->jump_flag[2] = 0;
         if (bar_reset) {
             ctr->bar.count = 0;
+            ctr->bar.abort = 0;
         }
     }
 }
@@ -314,7 +315,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         sa.ctr = ws.ctr;
         sa.status = status;
         sa.bin_cap = ws.bin_cap;
-        err = cudaMemsetAsync(&ws.ctr->bar.count, 0, sizeof(u32), s);
+        err = cudaMemsetAsync(&ws.ctr->bar, 0, 2 * sizeof(u32), s);
         if (err != cudaSuccess)
             return err;
         void* args[] = {&sa};

@@ -1,23 +1,39 @@
-// server.cu -- the serving entry points of include/appd.h.
+// server.cu -- the serving entry points of include/appd.h: continuous batching.
 //
-// Admission: a request for an n-vertex graph needs 8 n^2 bytes on the device
-// (its W and M slots).  It is admitted while the admitted total stays within
-// the budget (minus the solver workspace) and the in-flight count below the
-// limit; otherwise submit returns APPD_ERR_BUSY and the caller retries after
-// releasing finished requests.  Slots come from the stream-ordered allocator
-// on the server's stream, so admission and release never synchronize the
-// device.  Committed requests are handed to the solver in arrival order and
-// complete asynchronously; poll reports finished ones without blocking.
+// Admission: a request for an n-vertex graph needs 8 n^2 bytes of device
+// memory (its W and M slots).  It is admitted while the admitted total stays
+// within the budget (minus the server's fixed workspaces) and the in-flight
+// count below its limit; otherwise submit returns APPD_ERR_BUSY and the caller
+// retries after releasing finished requests.  Slots come from the
+// stream-ordered allocator.
+//
+// Dispatch: a server thread owns NSLOT stream slots, each with its own
+// batched-kernel runtime (workspace slices) and single-solve workspace, so
+// slots never share scratch.  Whenever a slot is free and requests are
+// committed, it takes every committed request as one batch: graphs up to the
+// size cut-over go through one persistent batched launch, larger ones through
+// the multi-CTA single-solve pipeline, all on that slot's stream, followed by
+// an event.  Requests committed while a batch runs wait for the next free
+// slot, so new work is admitted and launched while earlier work is still on
+// the GPU (the two slots' kernels overlap as SMs free up).  poll() retires
+// completed batches without blocking.
+#include <chrono>
+#include <condition_variable>
 #include <cstdint>
 #include <deque>
 #include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
 #include "../../include/appd.h"
 #include "internal.h"
 
+using namespace appd;
+
 namespace {
+
+constexpr int NSLOT = 2;
 
 struct Req {
     uint64_t id = 0;
@@ -28,21 +44,126 @@ struct Req {
     size_t bytes = 0;
     bool committed = false;
     bool done = false;
-    cudaEvent_t ev = nullptr;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    BatchRuntime* rt = nullptr;
+    Workspace* ws = nullptr;
+    bool busy = false;        // a batch is in flight and its event is recorded
+    bool launching = false;   // a batch is being enqueued (event not recorded yet)
+    std::vector<uint64_t> ids;
 };
 
 }  // namespace
 
 struct appd_server {
     std::mutex mu;
+    std::condition_variable cv;
     size_t budget = 0;
+    size_t reserved = 0;   // fixed workspaces
     size_t used = 0;
     int32_t max_inflight = 0;
     uint64_t next_id = 1;
-    cudaStream_t stream = nullptr;
+    int device = 0;
+    cudaStream_t alloc_stream = nullptr;
+    Slot slots[NSLOT];
     std::unordered_map<uint64_t, Req> reqs;
-    std::deque<uint64_t> pending;   // committed, not yet reported done
+    std::deque<uint64_t> pending;    // committed, not yet launched
+    std::deque<uint64_t> finished;   // completed, not yet reported by poll
+    std::thread dispatcher;
+    bool stop = false;
+    u32* status = nullptr;
+    BatchTuning tune;
+    appd_status error = APPD_OK;     // first dispatch error, reported by poll
 };
+
+namespace {
+
+// Moves requests of completed slots to `finished`.  Caller holds sv->mu.
+void retire(appd_server* sv)
+{
+    for (Slot& sl : sv->slots) {
+        if (!sl.busy || sl.launching)
+            continue;
+        cudaError_t q = cudaEventQuery(sl.done);
+        if (q == cudaErrorNotReady)
+            continue;
+        if (q != cudaSuccess && sv->error == APPD_OK)
+            sv->error = APPD_ERR_CUDA;
+        for (uint64_t id : sl.ids) {
+            auto it = sv->reqs.find(id);
+            if (it != sv->reqs.end()) {
+                it->second.done = true;
+                sv->finished.push_back(id);
+            }
+        }
+        sl.ids.clear();
+        sl.busy = false;
+    }
+}
+
+void dispatch_loop(appd_server* sv)
+{
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        retire(sv);
+        Slot* free_slot = nullptr;
+        bool any_busy = false;
+        for (Slot& sl : sv->slots) {
+            if (!sl.busy && !sl.launching && !free_slot)
+                free_slot = &sl;
+            any_busy |= sl.busy || sl.launching;
+        }
+        if (sv->stop && sv->pending.empty() && !any_busy)
+            return;
+        if (free_slot && !sv->pending.empty()) {
+            BatchDesc d;
+            std::vector<uint64_t> big;
+            std::vector<uint64_t> ids(sv->pending.begin(), sv->pending.end());
+            sv->pending.clear();
+            for (uint64_t id : ids) {
+                const Req& r = sv->reqs[id];
+                if (r.n <= sv->tune.n_split) {
+                    d.w.push_back(r.W);
+                    d.m.push_back(r.M);
+                    d.n.push_back((u32)r.n);
+                    d.dt.push_back((uint8_t)r.dt);
+                } else {
+                    big.push_back(id);
+                }
+            }
+            std::vector<Req> bigreq;
+            for (uint64_t id : big)
+                bigreq.push_back(sv->reqs[id]);
+            free_slot->launching = true;
+            free_slot->ids = ids;
+            lk.unlock();
+            cudaError_t e = batch_launch(*free_slot->rt, d, sv->status, free_slot->stream, false);
+            int st = APPD_OK;
+            for (const Req& r : bigreq) {
+                if (st != APPD_OK)
+                    break;
+                st = solve_on(*free_slot->ws, sv->status, r.W, r.n, (int)r.dt, r.M,
+                              free_slot->stream, false);
+            }
+            cudaError_t e2 = cudaEventRecord(free_slot->done, free_slot->stream);
+            lk.lock();
+            // only now may retire() look at the event: it belongs to this batch
+            free_slot->launching = false;
+            free_slot->busy = true;
+            if ((e != cudaSuccess || st != APPD_OK || e2 != cudaSuccess) && sv->error == APPD_OK)
+                sv->error = (st != APPD_OK) ? (appd_status)st : APPD_ERR_CUDA;
+            continue;
+        }
+        // nothing to launch: wait for a commit, or poll the busy slots
+        sv->cv.wait_for(lk, std::chrono::microseconds(any_busy ? 20 : 2000));
+    }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -53,10 +174,34 @@ appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_s
     appd_server* sv = new appd_server();
     sv->budget = budget_bytes;
     sv->max_inflight = max_inflight;
-    if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaGetDevice(&sv->device) != cudaSuccess) {
         delete sv;
         return APPD_ERR_CUDA;
     }
+    sv->status = device_status_word();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&sv->alloc_stream, cudaStreamNonBlocking);
+    for (Slot& sl : sv->slots) {
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = batch_runtime_create(sv->tune.n_split, sv->tune, &sl.rt);
+        if (e == cudaSuccess)
+            e = workspace_create(65536, &sl.ws);
+    }
+    if (e != cudaSuccess || !sv->status) {
+        appd_server_destroy(sv);
+        return e == cudaErrorMemoryAllocation ? APPD_ERR_NOMEM : APPD_ERR_CUDA;
+    }
+    size_t reserved = 0;
+    for (Slot& sl : sv->slots)
+        reserved += sl.ws->bytes + (size_t)batch_runtime_cap(sl.rt) * 4096;
+    sv->reserved = reserved;
+    sv->dispatcher = std::thread(dispatch_loop, sv);
     *out = sv;
     return APPD_OK;
 }
@@ -68,27 +213,34 @@ appd_status appd_server_submit(appd_server* sv, int64_t n, appd_dtype dt, uint64
         return APPD_ERR_INVALID;
     if (n > 65536)
         return APPD_ERR_TOO_LARGE;
-    std::lock_guard<std::mutex> lk(sv->mu);
     const size_t bytes = (size_t)n * (size_t)n * 4;
-    if ((int32_t)sv->reqs.size() >= sv->max_inflight || sv->used + 2 * bytes > sv->budget)
-        return APPD_ERR_BUSY;
     Req r;
-    r.id = sv->next_id++;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if ((int32_t)sv->reqs.size() >= sv->max_inflight ||
+            sv->reserved + sv->used + 2 * bytes > sv->budget)
+            return APPD_ERR_BUSY;
+        r.id = sv->next_id++;
+        sv->used += 2 * bytes;   // reserve before allocating
+    }
     r.n = n;
     r.dt = dt;
     r.bytes = bytes;
-    if (cudaMallocAsync(&r.W, bytes, sv->stream) != cudaSuccess)
-        return APPD_ERR_NOMEM;
-    if (cudaMallocAsync(&r.M, bytes, sv->stream) != cudaSuccess) {
-        cudaFreeAsync(r.W, sv->stream);
-        return APPD_ERR_NOMEM;
+    cudaError_t e = cudaMallocAsync(&r.W, bytes, sv->alloc_stream);
+    if (e == cudaSuccess)
+        e = cudaMallocAsync(&r.M, bytes, sv->alloc_stream);
+    // the caller may fill W from any stream: make the slot valid first
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(sv->alloc_stream);
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (e != cudaSuccess) {
+        if (r.W)
+            cudaFreeAsync(r.W, sv->alloc_stream);
+        if (r.M)
+            cudaFreeAsync(r.M, sv->alloc_stream);
+        sv->used -= 2 * bytes;
+        return e == cudaErrorMemoryAllocation ? APPD_ERR_NOMEM : APPD_ERR_CUDA;
     }
-    // the caller may fill W from another stream: make the slot valid first
-    if (cudaStreamSynchronize(sv->stream) != cudaSuccess)
-        return APPD_ERR_CUDA;
-    if (cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess)
-        return APPD_ERR_CUDA;
-    sv->used += 2 * bytes;
     *req_id = r.id;
     *W_slot = r.W;
     sv->reqs.emplace(r.id, r);
@@ -99,20 +251,17 @@ appd_status appd_server_commit(appd_server* sv, uint64_t req_id)
 {
     if (!sv)
         return APPD_ERR_INVALID;
-    std::lock_guard<std::mutex> lk(sv->mu);
-    auto it = sv->reqs.find(req_id);
-    if (it == sv->reqs.end())
-        return APPD_ERR_NOT_FOUND;
-    Req& r = it->second;
-    if (r.committed)
-        return APPD_ERR_INVALID;
-    appd_status st = appd_solve(r.W, r.n, r.dt, r.M, (appd_stream_t)sv->stream);
-    if (st != APPD_OK)
-        return st;
-    if (cudaEventRecord(r.ev, sv->stream) != cudaSuccess)
-        return APPD_ERR_CUDA;
-    r.committed = true;
-    sv->pending.push_back(req_id);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->reqs.find(req_id);
+        if (it == sv->reqs.end())
+            return APPD_ERR_NOT_FOUND;
+        if (it->second.committed)
+            return APPD_ERR_INVALID;
+        it->second.committed = true;
+        sv->pending.push_back(req_id);
+    }
+    sv->cv.notify_one();
     return APPD_OK;
 }
 
@@ -122,22 +271,21 @@ appd_status appd_server_poll(appd_server* sv, uint64_t* done_ids, const void** M
     if (!sv || !n_done || cap < 0 || (cap > 0 && (!done_ids || !M_ptrs)))
         return APPD_ERR_INVALID;
     std::lock_guard<std::mutex> lk(sv->mu);
+    retire(sv);
     int32_t k = 0;
-    while (k < cap && !sv->pending.empty()) {
-        uint64_t id = sv->pending.front();
-        Req& r = sv->reqs[id];
-        cudaError_t q = cudaEventQuery(r.ev);
-        if (q == cudaErrorNotReady)
-            break;
-        if (q != cudaSuccess)
-            return APPD_ERR_CUDA;
-        r.done = true;
+    while (k < cap && !sv->finished.empty()) {
+        const uint64_t id = sv->finished.front();
+        sv->finished.pop_front();
         done_ids[k] = id;
-        M_ptrs[k] = r.M;
+        M_ptrs[k] = sv->reqs[id].M;
         ++k;
-        sv->pending.pop_front();
     }
     *n_done = k;
+    if (sv->error != APPD_OK) {
+        appd_status e = sv->error;
+        sv->error = APPD_OK;
+        return e;
+    }
     return APPD_OK;
 }
 
@@ -152,9 +300,8 @@ appd_status appd_server_release(appd_server* sv, uint64_t req_id)
     Req& r = it->second;
     if (r.committed && !r.done)
         return APPD_ERR_BUSY;
-    cudaFreeAsync(r.W, sv->stream);
-    cudaFreeAsync(r.M, sv->stream);
-    cudaEventDestroy(r.ev);
+    cudaFreeAsync(r.W, sv->alloc_stream);
+    cudaFreeAsync(r.M, sv->alloc_stream);
     sv->used -= 2 * r.bytes;
     sv->reqs.erase(it);
     return APPD_OK;
@@ -164,14 +311,33 @@ appd_status appd_server_destroy(appd_server* sv)
 {
     if (!sv)
         return APPD_ERR_INVALID;
-    cudaStreamSynchronize(sv->stream);
-    for (auto& kv : sv->reqs) {
-        cudaFreeAsync(kv.second.W, sv->stream);
-        cudaFreeAsync(kv.second.M, sv->stream);
-        cudaEventDestroy(kv.second.ev);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        sv->pending.clear();   // committed but not launched: dropped
     }
-    cudaStreamSynchronize(sv->stream);
-    cudaStreamDestroy(sv->stream);
+    sv->cv.notify_all();
+    if (sv->dispatcher.joinable())
+        sv->dispatcher.join();
+    for (Slot& sl : sv->slots)
+        if (sl.stream)
+            cudaStreamSynchronize(sl.stream);
+    for (auto& kv : sv->reqs) {
+        cudaFreeAsync(kv.second.W, sv->alloc_stream);
+        cudaFreeAsync(kv.second.M, sv->alloc_stream);
+    }
+    if (sv->alloc_stream) {
+        cudaStreamSynchronize(sv->alloc_stream);
+        cudaStreamDestroy(sv->alloc_stream);
+    }
+    for (Slot& sl : sv->slots) {
+        batch_runtime_destroy(sl.rt);
+        workspace_destroy(sl.ws);
+        if (sl.done)
+            cudaEventDestroy(sl.done);
+        if (sl.stream)
+            cudaStreamDestroy(sl.stream);
+    }
     delete sv;
     return APPD_OK;
 }

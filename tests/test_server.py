@@ -1,0 +1,125 @@
+"""Serving: continuous batching under an HBM budget.
+
+Each request's result must be the same alone and in the mix (exact; every
+output is an input weight) and equal to the oracle."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2407_07058_gb300 import appd
+
+
+def _matrix(n, dt, seed):
+    if dt == appd.U32:
+        return synth.hash_u32(n, seed=seed)
+    return synth.euclid(synth.gmm_points(n, 2, 5, sigma=0.5, seed=seed, mean_box=10.0))
+
+
+def _fill(slot_ptr, W):
+    n = W.shape[0]
+    dt = appd.F32 if W.dtype == np.float32 else appd.U32
+    view = appd.device_view(slot_ptr, n, dt)
+    src = W if W.dtype == np.float32 else W.view(np.int32)
+    view.copy_(torch.from_numpy(src))
+    torch.cuda.synchronize()
+
+
+def _read(ptr, n, dtype):
+    dt = appd.F32 if dtype == np.float32 else appd.U32
+    return appd.device_view(ptr, n, dt).cpu().numpy().view(dtype)
+
+
+def _wait(sv, want, timeout=60.0):
+    got = {}
+    t0 = time.time()
+    while len(got) < want:
+        for rid, ptr in sv.poll():
+            got[rid] = ptr
+        assert time.time() - t0 < timeout, "server did not finish in time"
+        time.sleep(0.001)
+    return got
+
+
+@pytest.mark.gpu
+def test_server_alone_vs_mix_exact():
+    specs = [(64, appd.F32), (100, appd.U32), (2048, appd.F32), (300, appd.U32), (2500, appd.F32),
+             (8, appd.U32), (1000, appd.F32), (4100, appd.U32), (77, appd.F32)]
+    mats = [_matrix(n, dt, 500 + i) for i, (n, dt) in enumerate(specs)]
+    sv = appd.Server(4 << 30, 64)
+    try:
+        alone = []
+        for W, (n, dt) in zip(mats, specs):
+            rid, slot = sv.submit(n, dt)
+            _fill(slot, W)
+            sv.commit(rid)
+            done = _wait(sv, 1)
+            alone.append(_read(done[rid], n, W.dtype))
+            sv.release(rid)
+        # all at once, committed back to back while earlier batches run
+        ids = []
+        for W, (n, dt) in zip(mats, specs):
+            rid, slot = sv.submit(n, dt)
+            _fill(slot, W)
+            sv.commit(rid)
+            ids.append(rid)
+        done = _wait(sv, len(ids))
+        for rid, W, (n, dt), a in zip(ids, mats, specs, alone):
+            mix = _read(done[rid], n, W.dtype)
+            assert np.array_equal(mix.view(np.uint32), a.view(np.uint32)), f"n={n} alone != mix"
+            assert np.array_equal(mix.view(np.uint32), oracle.appd(W).view(np.uint32)), f"n={n}"
+            sv.release(rid)
+    finally:
+        sv.close()
+    assert appd.last_device_status() == 0
+
+
+@pytest.mark.gpu
+def test_server_admission_and_release_rules():
+    n = 1024
+    per = 2 * n * n * 4
+    sv = appd.Server(1 << 30, 4)   # room for the fixed workspaces plus a few requests
+    try:
+        got = []
+        while True:
+            r = sv.submit(n, appd.F32)
+            if r is None:
+                break
+            got.append(r)
+            assert len(got) <= 4
+        assert 1 <= len(got) <= 4          # budget or slot limit refused the next one
+        W = _matrix(n, appd.F32, 9)
+        rid, slot = got[0]
+        _fill(slot, W)
+        sv.commit(rid)
+        with pytest.raises(appd.AppdError):
+            sv.commit(rid)                 # committing twice is invalid
+        done = _wait(sv, 1)
+        assert np.array_equal(_read(done[rid], n, np.float32).view(np.uint32),
+                              oracle.appd(W).view(np.uint32))
+        for r2, _ in got:
+            sv.release(r2)
+        # after releasing, admission succeeds again
+        r = sv.submit(n, appd.F32)
+        assert r is not None
+        sv.release(r[0])
+        with pytest.raises(appd.AppdError):
+            sv.release(123456789)          # unknown id
+        del per
+    finally:
+        sv.close()
+
+
+def test_server_argument_errors_need_no_gpu():
+    lib = appd.load()
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.appd_server_create(0, 4, ctypes.byref(h)) == 1
+    assert lib.appd_server_create(1 << 30, 0, ctypes.byref(h)) == 1
+    assert lib.appd_server_submit(None, 10, 0, None, None) == 1
+    assert lib.appd_server_commit(None, 1) == 1
+    assert lib.appd_server_release(None, 1) == 1
+    assert lib.appd_server_destroy(None) == 1
