@@ -108,6 +108,24 @@ appd_status appd_solve_host(const void *W_host, int64_t n, appd_dtype dt, void *
                             appd_stream_t s);
 
 /*
+ * appd_solve_noalloc -- appd_solve for callers that cannot allocate device
+ * memory (a framework that owns a fixed pool or arena, an embedding that does
+ * not allow the driver's allocator once it is running).  No counterpart in
+ * the paper: it is the same result as appd_solve, for 0 <= n <= 1024, computed
+ * by one CTA with all scratch in a 4 MiB file-scope device array that the
+ * library carries on every device that loads it.
+ *   W, n, dt, M, s  as appd_solve; M == W is allowed.
+ * Returns APPD_ERR_TOO_LARGE for n > 1024 (the array's limit).  The call
+ * never allocates or frees memory.  The array is shared by all calls on a
+ * device and keeps the last call's contents (the kernel initialises what it
+ * reads); calls whose kernels overlap on the GPU race on it, so order them.
+ * The first call on a device looks up the array's address and sets a kernel
+ * attribute; make it before any stream capture.  Device-side consistency
+ * checks of this entry point are not reported by appd_last_device_status.
+ */
+appd_status appd_solve_noalloc(const void *W, int64_t n, appd_dtype dt, void *M, appd_stream_t s);
+
+/*
  * appd_mst -- the minimum spanning tree computed by the solve's MST stage.
  *   edges_out  device pointer to n-1 uint64 values; each is
  *              key << 32 | lo << 16 | hi, where lo < hi are the endpoints and

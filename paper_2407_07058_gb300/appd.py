@@ -22,7 +22,8 @@ STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD
           8: "APPD_ERR_ALIAS", 9: "APPD_ERR_NOT_FOUND", 10: "APPD_ERR_INTERNAL"}
 
 # every symbol that include/appd.h declares
-EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host", "appd_mst",
+EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host",
+           "appd_solve_noalloc", "appd_mst",
            "appd_leaf_order", "appd_solve_batched", "appd_batched_tuning", "appd_check_symmetric",
            "appd_last_device_status", "appd_probe_bounded_wait", "appd_release_workspaces",
            "appd_profile_begin",
@@ -55,6 +56,7 @@ def load(build_if_missing: bool = True):
             "appd_solve": [vp, i64, ci, vp, vp],
             "appd_solve_alg4": [vp, i64, ci, vp, vp],
             "appd_solve_host": [vp, i64, ci, vp, vp],
+            "appd_solve_noalloc": [vp, i64, ci, vp, vp],
             "appd_mst": [vp, i64, ci, vp, vp],
             "appd_leaf_order": [vp, i64, ci, vp, vp, vp],
             "appd_solve_batched": [vp, vp, vp, vp, vp, i32, vp],
