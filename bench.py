@@ -37,6 +37,8 @@ WORKLOADS = {
                                                  "in [0, 2^16), heavy ties"),
     "n1000": dict(n=1000, kind="gmm2", desc="single solve n=1000, FP32 Euclidean distances of "
                                              "2-D points, 5-component Gaussian mixture"),
+    "gmm16_16k": dict(n=16384, kind="gmm16", desc="single solve n=16384, FP32 Euclidean distances "
+                                                   "of 16-D points, 32-component Gaussian mixture"),
 }
 
 
@@ -157,8 +159,10 @@ def ncu_traffic(kernel: str):
         with open(path) as f:
             d = json.load(f)
         ent = d[kernel]
-        src = os.path.join(ROOT, ent["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for rel in ent["sources"]:
+            h.update(open(os.path.join(ROOT, rel), "rb").read())
+        h = h.hexdigest()[:16]
         if h != ent["source_sha256_16"]:
             return None
         return ent["bytes_per_launch_full"]
