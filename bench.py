@@ -191,26 +191,34 @@ def cpu_baseline(kind: str, n_full: int, budget_s: float = 12.0):
                       f"{total:.1f} s total, Prim + Algorithm 4, one thread"}
 
 
-def bench_batched(steps: int, warmup: int, dev):
+def bench_batched(steps: int, warmup: int, dev, rank: int = 0, world: int = 1):
     """4096 graphs, n = floor(32 * 64^u) clipped to [32, 2048], FP32 uniform(0,1)
-    weights seeded per graph: one batched call vs 4096 plain solves."""
+    weights seeded per graph: one batched call vs one plain solve per graph.
+    With N ranks each solves its shard of the graphs (weak scaling by graphs)."""
     import torch
 
     import synth
-    from paper_2407_07058_gb300 import appd
-    sizes = [int(x) for x in synth.cfg4_sizes(4096)]
+    from paper_2407_07058_gb300 import appd, replicas
+    all_sizes = [int(x) for x in synth.cfg4_sizes(4096)]
+    mine = replicas.rank_graphs(all_sizes, rank, world)
+    sizes = [all_sizes[g] for g in mine]
     offs = np.cumsum([0] + [n * n for n in sizes])[:-1].astype(np.int64)
     total = int(offs[-1] + sizes[-1] ** 2)
     W = torch.empty(total, dtype=torch.float32, device=dev)
     M = torch.empty_like(W)
     st = torch.cuda.current_stream()
-    for g, n in enumerate(sizes):
-        synth.device_uniform01(synth.cfg4_seed(g), n, W.data_ptr() + 4 * int(offs[g]), st.cuda_stream)
+    for k, g in enumerate(mine):
+        synth.device_uniform01(synth.cfg4_seed(g), sizes[k], W.data_ptr() + 4 * int(offs[k]),
+                               st.cuda_stream)
     torch.cuda.synchronize()
+    # parameters searched on this GPU (cached beside the built library)
+    tuning = appd.batched_autotune(os.path.join(os.path.dirname(appd.__file__), "_build",
+                                                "tuning.jsonl"))
     for _ in range(max(1, warmup)):
         appd.solve_batched(W, offs, sizes, out=M)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    replicas.barrier()
     appd.profile_begin()
     e0.record(st)
     for _ in range(steps):
@@ -218,7 +226,8 @@ def bench_batched(steps: int, warmup: int, dev):
     e1.record(st)
     torch.cuda.synchronize()
     prof = appd.profile_end()
-    ms_b = e0.elapsed_time(e1) / steps
+    replicas.barrier()
+    ms_b = replicas.max_over_ranks(e0.elapsed_time(e1) / steps, dev)
     # one by one: 4096 plain solves on the same stream
     views = [(W[o: o + n * n].view(n, n), M[o: o + n * n].view(n, n)) for o, n in zip(offs, sizes)]
     for w, m in views[:64]:
@@ -229,16 +238,17 @@ def bench_batched(steps: int, warmup: int, dev):
         appd.solve(w, out=m)
     e1.record(st)
     torch.cuda.synchronize()
-    ms_1 = e0.elapsed_time(e1)
+    ms_1 = replicas.max_over_ranks(e0.elapsed_time(e1), dev)
     if appd.last_device_status() != 0:
         raise RuntimeError("device status error in the batched run")
-    ent = float(sum(n * n for n in sizes))
+    ent = float(sum(n * n for n in all_sizes))
+    G = len(all_sizes)
     return {"workload": "4096 graphs, n log-uniform in [32, 2048], FP32 uniform(0,1) weights",
-            "graphs": len(sizes), "ms_per_batch": ms_b, "graphs_per_s": len(sizes) / (ms_b / 1e3),
-            "entries_per_s": ent / (ms_b / 1e3),
-            "one_by_one_ms": ms_1, "one_by_one_graphs_per_s": len(sizes) / (ms_1 / 1e3),
+            "graphs": G, "graphs_per_rank": len(sizes), "ms_per_batch": ms_b,
+            "graphs_per_s": G / (ms_b / 1e3), "entries_per_s": ent / (ms_b / 1e3),
+            "one_by_one_ms": ms_1, "one_by_one_graphs_per_s": G / (ms_1 / 1e3),
             "speedup_vs_one_by_one": ms_1 / ms_b, "kernel_launches_per_batch": prof["launches"] / steps,
-            "bytes_w_plus_m": 8.0 * ent}
+            "bytes_w_plus_m": 8.0 * ent, "tuning": tuning}
 
 
 def serving_requests(count: int, seed: int = 5):
@@ -377,16 +387,14 @@ def run_ours(args, rank, world, local):
     import torch.distributed as dist
 
     import synth
-    from paper_2407_07058_gb300 import appd
+    from paper_2407_07058_gb300 import appd, replicas
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = replicas.barrier
 
     wl = WORKLOADS[args.workload]
     n, kind = wl["n"], wl["kind"]
@@ -424,10 +432,7 @@ def run_ours(args, rank, world, local):
     ms = ev0.elapsed_time(ev1)
     if appd.last_device_status() != 0:
         raise RuntimeError("device status error in the timed region")
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, dev)
     ms_step = ms / args.steps
     value = world * args.steps * n * n / (ms / 1e3)
 
@@ -463,7 +468,7 @@ def run_ours(args, rank, world, local):
         t0 = time.perf_counter()
         for _ in range(ke):
             appd.solve_host_ptr(Wh.data_ptr(), n, dt_code, Mh.data_ptr())
-        te = time.perf_counter() - t0
+        te = replicas.max_over_ranks(time.perf_counter() - t0, dev)
         barrier()
         e2e = {"value": world * ke * n * n / te, "unit": "entries/s",
                "h2d_bytes_per_step": 4 * n * n, "d2h_bytes_per_step": 4 * n * n,
@@ -477,7 +482,7 @@ def run_ours(args, rank, world, local):
     if not args.no_batched:
         del W, M
         torch.cuda.empty_cache()
-        batched = bench_batched(max(3, min(args.steps, 10)), args.warmup, dev)
+        batched = bench_batched(max(3, min(args.steps, 10)), args.warmup, dev, rank, world)
     serving = None
     if not args.no_serving:
         torch.cuda.empty_cache()

@@ -176,6 +176,23 @@ appd_status appd_solve_batched(const int64_t *offsets, const void *Ws, const int
 appd_status appd_batched_tuning(int32_t ctas_per_sm, int32_t fill_rows, int64_t n_split);
 
 /*
+ * appd_batched_autotune -- picks the batched path's fill rows and size
+ * cut-over for this GPU by timing every candidate pair (fill rows 64..512,
+ * cut-over 512..4096) on a seeded synthetic batch of 192 graphs, installs the
+ * fastest for this process, and appends it to the JSON-lines file cache_path
+ * (keyed by GPU name and driver version; NULL: no cache).  If cache_path
+ * already holds an entry for this GPU, it is installed without a search.
+ * Synchronizes s; allocates 2.4 GB of device memory for the search and frees
+ * it before returning.  APPD_ERR_CUDA when no device answers.  (Scheduling parameters of
+ * this library; no counterpart in the paper.)
+ */
+appd_status appd_batched_autotune(const char *cache_path, appd_stream_t s);
+
+/* Reads the batched path's current parameters (see appd_batched_tuning);
+ * APPD_ERR_INVALID on a null pointer.  Needs no GPU. */
+appd_status appd_batched_get_tuning(int32_t *ctas_per_sm, int32_t *fill_rows, int64_t *n_split);
+
+/*
  * appd_check_symmetric -- returns APPD_OK if W(i,j) and W(j,i) have identical
  * bits for all i < j, APPD_ERR_ASYMMETRIC otherwise.  Synchronizes s.
  */

@@ -24,7 +24,8 @@ STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD
 # every symbol that include/appd.h declares
 EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host",
            "appd_solve_noalloc", "appd_mst",
-           "appd_leaf_order", "appd_solve_batched", "appd_batched_tuning", "appd_check_symmetric",
+           "appd_leaf_order", "appd_solve_batched", "appd_batched_tuning", "appd_batched_autotune",
+           "appd_batched_get_tuning", "appd_check_symmetric",
            "appd_last_device_status", "appd_probe_bounded_wait", "appd_release_workspaces",
            "appd_profile_begin",
            "appd_profile_end", "appd_server_create",
@@ -61,6 +62,9 @@ def load(build_if_missing: bool = True):
             "appd_leaf_order": [vp, i64, ci, vp, vp, vp],
             "appd_solve_batched": [vp, vp, vp, vp, vp, i32, vp],
             "appd_batched_tuning": [i32, i32, i64],
+            "appd_batched_autotune": [ctypes.c_char_p, vp],
+            "appd_batched_get_tuning": [ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                        ctypes.POINTER(i64)],
             "appd_check_symmetric": [vp, i64, ci, vp],
             "appd_last_device_status": [vp],
             "appd_probe_bounded_wait": [i32, vp],
@@ -228,6 +232,20 @@ def batched_tuning(ctas_per_sm: int = 1, fill_rows: int = 256, n_split: int = 20
 def probe_bounded_wait(limit_ms: int = 200, stream=None):
     """Run a grid-barrier wait out on purpose (bounded; see appd.h)."""
     _check(load().appd_probe_bounded_wait(limit_ms, _stream_ptr(stream)), "appd_probe_bounded_wait")
+
+
+def batched_autotune(cache_path: str | None = None, stream=None) -> dict:
+    """Search the batched path's parameters on this GPU (cached in cache_path)."""
+    arg = None if cache_path is None else cache_path.encode()
+    _check(load().appd_batched_autotune(arg, _stream_ptr(stream)), "appd_batched_autotune")
+    return get_batched_tuning()
+
+
+def get_batched_tuning() -> dict:
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().appd_batched_get_tuning(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "appd_batched_get_tuning")
+    return {"ctas_per_sm": a.value, "fill_rows": b.value, "n_split": c.value}
 
 
 def release_workspaces():

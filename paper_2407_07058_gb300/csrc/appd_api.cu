@@ -375,6 +375,12 @@ int appd::solve_on(Workspace& ws, u32* status, const void* W, int64_t n, int dt,
     return (int)solve_with(ws, status, W, n, dt, M, s, alg4);
 }
 
+BatchTuning appd::current_batch_tuning()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_tune;
+}
+
 u32* appd::device_status_word()
 {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -105,6 +105,9 @@ struct BatchTuning {
         return ctas_per_sm == o.ctas_per_sm && fill_rows == o.fill_rows && n_split == o.n_split;
     }
 };
+// the batched path's current parameters (appd_batched_tuning)
+BatchTuning current_batch_tuning();
+
 // host description of one batch of small graphs
 struct BatchDesc {
     std::vector<const void*> w;

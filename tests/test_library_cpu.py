@@ -52,6 +52,16 @@ def test_argument_errors_need_no_gpu():
     assert lib.appd_leaf_order(fake, 70000, 0, fake2, fake2, None) == 2
     assert lib.appd_check_symmetric(None, 4, 0, None) == 1
     assert lib.appd_solve_batched(None, None, None, None, None, -1, None) == 1
+    assert lib.appd_batched_get_tuning(None, None, None) == 1
+
+
+def test_tuning_readback_needs_no_gpu():
+    appd.batched_tuning(1, 128, 1024)
+    try:
+        assert appd.get_batched_tuning() == {"ctas_per_sm": 1, "fill_rows": 128, "n_split": 1024}
+    finally:
+        appd.batched_tuning()
+    assert appd.get_batched_tuning() == {"ctas_per_sm": 1, "fill_rows": 256, "n_split": 2048}
 
 
 def test_build_is_in_tree_for_sm103a():
