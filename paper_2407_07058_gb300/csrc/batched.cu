@@ -52,38 +52,260 @@ struct BatchArgs {
     SliceWs* slices;
     u32* status;
     u32 bin_cap;          // u64 bins that fit the dynamic shared memory
+    u32 warp_bins;        // u64 bins per warp when each warp owns a group
     u32 fill_rows;        // rows per fill tile
 };
 
 constexpr int BATCH_THREADS = 512;
 
-// Round-1 row minima of one graph by one CTA (each warp a row).
+// Column groups of a row that starts at any 4-byte boundary.
+//
+// out[u] = columns [4g, 4g + 4) of the row for g = g0 + 32u, where g0 is the
+// calling lane's first group (the warp covers 32 * U consecutive groups).
+// Every group costs one aligned 16-byte load: when the row is not 16-byte
+// aligned, a group's upper columns sit in the next aligned block, which the
+// neighbouring lane loaded (lane 31 takes lane 0's next block, or loads one
+// extra block past the warp's range).  Blocks not wholly inside [lo, hi) --
+// only at the two ends of the matrix -- are read element by element, so no
+// load leaves the matrix.  Columns >= n hold other rows' values (or 0): the
+// caller masks them.  All 32 lanes must call it together.
+template <int U>
+__device__ __forceinline__ void load_groups(const u32* row, u32 n, const u32* lo, const u32* hi, u32 g0,
+                                            uint4 (&out)[U])
+{
+    const u32 lane = threadIdx.x & 31;
+    const u32 s = (u32)(((uintptr_t)row >> 2) & 3u);
+    const u32* base = row - s;            // 16-byte aligned
+    const u32 nb = (n + s + 3) >> 2;      // aligned blocks that hold the row
+    auto blk = [&](u32 bi) -> uint4 {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (bi < nb) {
+            const u32* p = base + 4 * (size_t)bi;
+            if (p >= lo && p + 4 <= hi) {
+                v = ld_stream_v4(p);
+            } else {
+                v.x = (p >= lo && p < hi) ? ld_stream_u32(p) : 0u;
+                v.y = (p + 1 >= lo && p + 1 < hi) ? ld_stream_u32(p + 1) : 0u;
+                v.z = (p + 2 >= lo && p + 2 < hi) ? ld_stream_u32(p + 2) : 0u;
+                v.w = (p + 3 >= lo && p + 3 < hi) ? ld_stream_u32(p + 3) : 0u;
+            }
+        }
+        return v;
+    };
+    uint4 bk[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        bk[u] = blk(g0 + 32 * u);
+    if (s == 0) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            out[u] = bk[u];
+        return;
+    }
+    const uint4 extra = (lane == 31) ? blk(g0 + 32 * (U - 1) + 1) : make_uint4(0u, 0u, 0u, 0u);
+    const int src = (lane + 1) & 31;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        uint4 nx;
+        nx.x = __shfl_sync(0xFFFFFFFFu, bk[u].x, src);
+        nx.y = __shfl_sync(0xFFFFFFFFu, bk[u].y, src);
+        nx.z = __shfl_sync(0xFFFFFFFFu, bk[u].z, src);
+        uint4 nl = extra;
+        if (u + 1 < U) {
+            nl.x = __shfl_sync(0xFFFFFFFFu, bk[u + 1 < U ? u + 1 : u].x, 0);
+            nl.y = __shfl_sync(0xFFFFFFFFu, bk[u + 1 < U ? u + 1 : u].y, 0);
+            nl.z = __shfl_sync(0xFFFFFFFFu, bk[u + 1 < U ? u + 1 : u].z, 0);
+        }
+        if (lane == 31)
+            nx = nl;
+        const uint4 c = bk[u];
+        out[u] = (s == 1) ? make_uint4(c.y, c.z, c.w, nx.x)
+                          : (s == 2) ? make_uint4(c.z, c.w, nx.x, nx.y) : make_uint4(c.w, nx.x, nx.y, nx.z);
+    }
+}
+
+// Round-1 row minima of one graph by one CTA: each warp takes a row and
+// keeps eight 16-byte loads per lane in flight (64 KB per CTA).
 template <int DT>
 __device__ void rowmin_cta(const u32* __restrict__ W, u32 n, u64* __restrict__ best)
 {
+    constexpr int U = 8;
     const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const u32* hi = W + (size_t)n * n;
+    const u32 ng = (n + 3) >> 2;
     for (u32 i = w; i < n; i += nw) {
         const u32* r = W + (size_t)i * n;
         u64 m = EDGE_INF;
-        u32 j = lane;
-        for (; j + 96 < n; j += 128) {
-            const u32 b0 = ld_stream_u32(r + j), b1 = ld_stream_u32(r + j + 32);
-            const u32 b2 = ld_stream_u32(r + j + 64), b3 = ld_stream_u32(r + j + 96);
-            const u64 c0 = ((u64)key_of(b0, DT) << 32) | j, c1 = ((u64)key_of(b1, DT) << 32) | (j + 32);
-            const u64 c2 = ((u64)key_of(b2, DT) << 32) | (j + 64), c3 = ((u64)key_of(b3, DT) << 32) | (j + 96);
-            if (j != i && c0 < m) m = c0;
-            if (j + 32 != i && c1 < m) m = c1;
-            if (j + 64 != i && c2 < m) m = c2;
-            if (j + 96 != i && c3 < m) m = c3;
-        }
-        for (; j < n; j += 32) {
-            const u64 c = ((u64)key_of(ld_stream_u32(r + j), DT) << 32) | j;
-            if (j != i && c < m)
-                m = c;
+        for (u32 c0 = 0; c0 < ng; c0 += 32 * U) {
+            uint4 v[U];
+            load_groups<U>(r, n, W, hi, c0 + lane, v);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const u32 j = 4 * (c0 + lane + 32 * u);
+                const u32 x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const u64 c = ((u64)key_of(x[t], DT) << 32) | (j + t);
+                    if (j + t < n && j + t != i && c < m)
+                        m = c;
+                }
+            }
         }
         m = warp_min_u64(m);
         if (lane == 0)
             best[i] = pack_edge((u32)(m >> 32), i, (u32)m & 0xFFFFu);
+    }
+}
+
+// Sorts up to four uniform row ids ascending; slots past np repeat the
+// smallest row (same key, same row: such a slot never changes a minimum).
+__device__ __forceinline__ void sort_rows4(u32* rid, u32 np)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if ((u32)q >= np)
+            rid[q] = 0xFFFFFFFFu;
+    auto cs = [&](int a, int c) {
+        const u32 lo = min(rid[a], rid[c]), hi = max(rid[a], rid[c]);
+        rid[a] = lo;
+        rid[c] = hi;
+    };
+    cs(0, 1);
+    cs(2, 3);
+    cs(0, 2);
+    cs(1, 3);
+    cs(1, 2);
+#pragma unroll
+    for (int q = 1; q < 4; ++q)
+        if ((u32)q >= np)
+            rid[q] = rid[0];
+}
+
+// One contraction level with one warp per group: warp w folds every row of
+// group A (A = w, w + warps, ...) into its own cn bins in shared memory, then
+// writes row A of C_{r+1} (row stride sout) and A's row minimum.  Groups
+// proceed concurrently and independently (no block barrier between groups),
+// so 16 groups' loads are in flight instead of one item's.  Level 0 reads W
+// rows at any alignment (load_groups); later levels read C_r with row stride
+// sin.  Needs cn <= the per-warp capacity.
+template <int DT, int LEVEL0>
+__device__ void contract_level_warps(const ContractArgs& a, u32 cr, u32 cn, u32 sin, u32 sout,
+                                     const u32* wlo, const u32* whi, u64* wbins, u32 wcap)
+{
+    const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    u64* bins = wbins + (size_t)wid * wcap;
+    for (u32 A = wid; A < cn; A += nw) {
+        for (u32 b = lane; b < cn; b += 32)
+            bins[b] = EDGE_INF;
+        __syncwarp();
+        const u32 m0 = a.gstart[A], m1 = a.gstart[A + 1];
+        for (u32 p = m0; p < m1; p += 4) {
+            const u32 np = min(4u, m1 - p);
+            u32 rid[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                rid[q] = a.members[p + ((u32)q < np ? q : 0)];
+            if (LEVEL0) {
+                constexpr int U = 2;
+                sort_rows4(rid, np);
+                const u32* W = (const u32*)a.cin;
+                const u32 ng = (cr + 3) >> 2;
+                for (u32 c0 = 0; c0 < ng; c0 += 32 * U) {
+                    uint4 v[4][U];
+                    load_groups<U>(W + (size_t)rid[0] * cr, cr, wlo, whi, c0 + lane, v[0]);
+#pragma unroll
+                    for (int q = 1; q < 4; ++q) {
+                        if ((u32)q < np) {
+                            load_groups<U>(W + (size_t)rid[q] * cr, cr, wlo, whi, c0 + lane, v[q]);
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < U; ++u)
+                                v[q][u] = v[0][u];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const u32 g = c0 + lane + 32 * u;
+                        uint4 lab = make_uint4(A, A, A, A);
+                        if (g < ng) {
+                            lab = *reinterpret_cast<const uint4*>(a.label + 4 * g);
+                            if (4 * g + 1 >= cr)
+                                lab.y = A;
+                            if (4 * g + 2 >= cr)
+                                lab.z = A;
+                            if (4 * g + 3 >= cr)
+                                lab.w = A;
+                        }
+                        const uint4 x[4] = {v[0][u], v[1][u], v[2][u], v[3][u]};
+                        fold_group<DT, 4, true>(x, rid, 4 * g, lab, A, 0, cn, bins);
+                    }
+                }
+            } else {
+                const u64* C = (const u64*)a.cin;
+                const u64* rp[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    rp[q] = C + (size_t)rid[q] * sin;
+                auto update = [&](u32 L, u64 e) {
+                    if (L != A && e < bins[L])
+                        atomicMin(&bins[L], e);
+                };
+                u32 jt = 0;
+                if (((sin & 1u) == 0) && (((uintptr_t)C & 15u) == 0)) {
+                    const u32 n2 = cr >> 1;
+                    for (u32 g0 = lane; g0 < n2; g0 += 64) {
+                        uint4 v[2][4];
+                        uint2 lab[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const u32 g = g0 + 32 * u;
+                            const bool ok = g < n2;
+                            v[u][0] = ok ? ld_stream_v4(rp[0] + 2 * g) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                            for (int q = 1; q < 4; ++q)
+                                v[u][q] = (ok && (u32)q < np) ? ld_stream_v4(rp[q] + 2 * g) : v[u][0];
+                            lab[u] = ok ? *reinterpret_cast<const uint2*>(a.label + 2 * g) : make_uint2(A, A);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            u64 e0 = EDGE_INF, e1 = EDGE_INF;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const u64 x0 = ((u64)v[u][q].y << 32) | v[u][q].x;
+                                const u64 x1 = ((u64)v[u][q].w << 32) | v[u][q].z;
+                                e0 = x0 < e0 ? x0 : e0;
+                                e1 = x1 < e1 ? x1 : e1;
+                            }
+                            update(lab[u].x, e0);
+                            update(lab[u].y, e1);
+                        }
+                    }
+                    jt = 2 * n2;
+                }
+                for (u32 j = jt + lane; j < cr; j += 32) {
+                    u64 e = rp[0][j];
+#pragma unroll
+                    for (int q = 1; q < 4; ++q)
+                        if ((u32)q < np) {
+                            const u64 x = rp[q][j];
+                            e = x < e ? x : e;
+                        }
+                    update(a.label[j], e);
+                }
+            }
+        }
+        __syncwarp();
+        u64 m = EDGE_INF;
+        u64* dst = a.cout + (size_t)A * sout;
+        for (u32 b = lane; b < cn; b += 32) {
+            const u64 v = bins[b];
+            dst[b] = v;
+            m = v < m ? v : m;
+        }
+        m = warp_min_u64(m);
+        if (lane == 0 && m != EDGE_INF)
+            atomicMin(&a.best_out[A], m);
+        __syncwarp();
     }
 }
 
@@ -112,13 +334,17 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, const B
     }
     rowmin_cta<DT>(W, n, w.best0);
     __syncthreads();
+    const bool vec = (n % 4 == 0) && (((uintptr_t)W & 15u) == 0);
 
     // contraction scratch: M (16-byte aligned start) unless solving in place
     const u32 h = n / 2;
     u64* cb0 = (M == W) ? w.cscratch : (u64*)(((uintptr_t)M + 15) & ~(uintptr_t)15);
     u64* cb1 = (u64*)((char*)cb0 + (((size_t)h * h * sizeof(u64) + 15) & ~(size_t)15));
-    const bool vec = (n % 4 == 0) && (((uintptr_t)W & 15u) == 0);
     const int levels = ceil_log2_dev(n);
+    // row stride of C_r: the warp-per-group contraction pads odd widths to
+    // even (16-byte aligned rows) where the scratch half has room
+    u32 stride = n;
+    const size_t cap_half[2] = {(size_t)h * h, (size_t)(n / 4) * (n / 4)};
     for (int r = 0; r < levels; ++r) {
         StepArgs sa;
         sa.level = r;
@@ -162,9 +388,20 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, const B
         ca.ctr = ctr;
         ca.bin_cap = b.bin_cap;
         const u32 cr = ((volatile u32*)ctr->c)[r], cn = ((volatile u32*)ctr->c)[r + 1];
+        u64* bins = reinterpret_cast<u64*>(smem);
+        if (cn <= b.warp_bins) {
+            const u32 sout = ((cn & 1u) && (size_t)cn * (cn + 1) <= cap_half[r & 1]) ? cn + 1 : cn;
+            if (r == 0)
+                contract_level_warps<DT, 1>(ca, cr, cn, stride, sout, W, W + (size_t)n * n, bins, b.warp_bins);
+            else
+                contract_level_warps<DT, 0>(ca, cr, cn, stride, sout, W, W, bins, b.warp_bins);
+            stride = sout;
+            __syncthreads();
+            continue;
+        }
+        stride = cn;
         const u32 tc = *(volatile u32*)&ctr->total_chunks;
         const u32 total = tc * *(volatile u32*)&ctr->nbr;
-        u64* bins = reinterpret_cast<u64*>(smem);
         for (u32 item = 0; item < total; ++item) {
             if (r == 0) {
                 if (vec)
@@ -267,6 +504,7 @@ struct BatchRuntime {
     size_t desc_bytes = 0;
     size_t smem = 0;
     u32 bin_cap = 0;
+    u32 warp_bins = 0;
     struct Plan {
         void* dev = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -380,6 +618,7 @@ BatchArgs make_args(const BatchRuntime& rt, void* dev, const size_t off[5], u32 
     a.slices = rt.d_slices;
     a.status = status;
     a.bin_cap = rt.bin_cap;
+    a.warp_bins = rt.warp_bins;
     a.fill_rows = (u32)rt.tune.fill_rows;
     return a;
 }
@@ -417,9 +656,12 @@ cudaError_t batch_runtime_create(int64_t cap, const BatchTuning& tune, BatchRunt
         e = cudaMemcpy(nr->d_slices, hs.data(), sizeof(SliceWs) * nr->nslices, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMalloc(&nr->d_next, 256);
-    // dynamic shared memory: the fill tile (the contraction bins fit inside it)
-    nr->smem = fill_smem_bytes((u32)tune.fill_rows);
+    // dynamic shared memory: the fill tile, or per-warp contraction bins for
+    // up to 1024 groups, whichever is larger (the phases reuse it in turn)
+    nr->smem = std::max(fill_smem_bytes((u32)tune.fill_rows),
+                        (size_t)(BATCH_THREADS / 32) * 1024 * sizeof(u64));
     nr->bin_cap = (u32)(nr->smem / sizeof(u64));
+    nr->warp_bins = (u32)(nr->bin_cap / (BATCH_THREADS / 32));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nr->smem);
     if (e != cudaSuccess) {
