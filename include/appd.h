@@ -168,7 +168,7 @@ appd_status appd_solve_batched(const int64_t *offsets, const void *Ws, const int
 /*
  * appd_batched_tuning -- sets the batched path's parameters for this process:
  *   ctas_per_sm  persistent CTAs per SM (1 or 2), each with its own workspace;
- *   fill_rows    rows per fill tile inside a CTA (64, 128, 256 or 512);
+ *   fill_rows    rows per fill batch inside a CTA (a power of two, 64..2048);
  *   n_split      graphs with n > n_split go through the single-solve pipeline.
  * Defaults: 1, 256, 2048.  Returns APPD_ERR_INVALID for values out of range.
  * (No counterpart in the paper: scheduling parameters of this library.)

@@ -620,8 +620,8 @@ appd_status appd_solve_batched(const int64_t* offsets, const void* Ws, const int
 
 appd_status appd_batched_tuning(int32_t ctas_per_sm, int32_t fill_rows, int64_t n_split)
 {
-    if (ctas_per_sm < 1 || ctas_per_sm > 2 || (fill_rows != 64 && fill_rows != 128 &&
-                                               fill_rows != 256 && fill_rows != 512) ||
+    if (ctas_per_sm < 1 || ctas_per_sm > 2 || fill_rows < 64 || fill_rows > 2048 ||
+        (fill_rows & (fill_rows - 1)) != 0 ||
         n_split < 1 || n_split > 65536)
         return APPD_ERR_INVALID;
     std::lock_guard<std::mutex> lk(g_mu);

@@ -455,10 +455,10 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, const B
     leaf_body(t, la);
     __syncthreads();
 
-    const u32 fr = b.fill_rows;
+    // one column block at a time, all rows (in batches of fill_rows): the
+    // block's sort and table are built once
     for (u32 j0 = 0; j0 < n; j0 += FC)
-        for (u32 r0 = 0; r0 < n; r0 += fr)
-            fill_tile<DT>(w.pos, w.st, n, j0, r0, min(fr, n - r0), fr, M, smem);
+        fill_tile<DT>(w.pos, w.st, n, j0, 0, n, b.fill_rows, M, smem);
 }
 
 __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)

@@ -23,7 +23,6 @@ __device__ __forceinline__ u32 rmq_gap(const u32* __restrict__ st, u32 stride, u
 // dynamic shared memory layout of k_fill
 struct FillSmem {
     u32 T[FC + 1][FC];   // T[t][col]: running max of A outward from split t
-    u64 sort[FC];
     u32 q[FC];           // sorted column positions
     u32 col[FC];         // sorted index -> column offset
     u32 rank[FC];        // column offset -> sorted index
@@ -36,11 +35,11 @@ inline size_t fill_smem_bytes(u32 rows_per_cta) { return sizeof(FillSmem) + (siz
 // value at the column with sorted index k is max(R_p, A[t..k-1]) for k >= t
 // and max(L_p, A[k..t-2]) for k < t, where R_p / L_p are the largest gaps
 // from p to the nearest column on each side.  The A-parts depend only on
-// (t, k): they form the table T, built once per CTA, so each output element
+// (t, k): they form the table T, built once per tile, so each output element
 // costs one shared load, one max and the key-to-bits transform.
-// One tile: columns [j0, j0+FC) x rows [r0, r0+nr).  smem_raw holds a
-// FillSmem followed by 3 * rows_cap u32 (nr <= rows_cap); every thread of the
-// CTA (>= FC + 1 threads) calls it.
+// One tile: columns [j0, j0+FC) x rows [r0, r0+nr), the rows in batches of
+// rows_cap.  smem_raw holds a FillSmem followed by 3 * rows_cap u32; every
+// thread of the CTA (>= FC + 1 threads) calls it.
 template <int DT>
 __device__ __forceinline__ void fill_tile(const u32* __restrict__ pos, const u32* __restrict__ st,
                                           u32 n, u32 j0, u32 r0, u32 nr, u32 rows_cap,
@@ -53,108 +52,107 @@ __device__ __forceinline__ void fill_tile(const u32* __restrict__ pos, const u32
     const u32 tid = threadIdx.x, nthr = blockDim.x;
     const u32 nc = min((u32)FC, n - j0);
 
-    // 1. sort the tile's column positions (bitonic, FC elements)
+    // 1. sort the tile's column positions: positions are distinct, so a
+    //    column's sorted index is the number of smaller positions
     if (tid < FC)
-        S.sort[tid] = ((u64)(tid < nc ? __ldg(pos + j0 + tid) : 0xFFFFFFFFu) << 32) | tid;
+        S.q[tid] = tid < nc ? __ldg(pos + j0 + tid) : 0xFFFFFFFFu;
     __syncthreads();
-    for (u32 k = 2; k <= FC; k <<= 1) {
-        for (u32 j = k >> 1; j > 0; j >>= 1) {
-            if (tid < FC) {
-                u32 ixj = tid ^ j;
-                if (ixj > tid) {
-                    bool up = (tid & k) == 0;
-                    u64 x = S.sort[tid], y = S.sort[ixj];
-                    if ((x > y) == up) {
-                        S.sort[tid] = y;
-                        S.sort[ixj] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (tid < FC) {
-        u64 e = S.sort[tid];
-        S.q[tid] = (u32)(e >> 32);
-        S.col[tid] = (u32)e;
-        if (tid < nc)
-            S.rank[(u32)e] = tid;
+    if (tid < nc) {
+        const u32 p = S.q[tid];
+        u32 k = 0;
+#pragma unroll 8
+        for (u32 c = 0; c < nc; ++c)
+            k += S.q[c] < p;
+        S.rank[tid] = k;
+        S.A[k] = p;       // A holds the sorted positions until step 2
     }
     __syncthreads();
-    // 2. gaps between consecutive sorted columns; row split points and sides
+    if (tid < nc) {
+        S.col[S.rank[tid]] = tid;
+        S.q[tid] = S.A[tid];
+    }
+    __syncthreads();
+    // 2. gaps between consecutive sorted columns
+    u32 gap = 0;
     if (tid + 1 < nc)
-        S.A[tid] = rmq_gap(st, n, S.q[tid], S.q[tid + 1] - 1);
-    for (u32 r = tid; r < nr; r += nthr) {
-        u32 p = __ldg(pos + r0 + r);
-        u32 lo = 0, hi = nc;
-        while (lo < hi) {
-            u32 mid = (lo + hi) >> 1;
-            if (S.q[mid] < p)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        s_t[r] = lo;
-        s_L[r] = lo > 0 ? rmq_gap(st, n, S.q[lo - 1], p - 1) : 0u;
-        s_R[r] = (lo < nc && S.q[lo] != p) ? rmq_gap(st, n, p, S.q[lo] - 1) : 0u;
-    }
+        gap = rmq_gap(st, n, S.q[tid], S.q[tid + 1] - 1);
     __syncthreads();
-    // 3. the table: row t holds the running maxima outward from split t
-    if (tid <= nc) {
-        const u32 t = tid;
+    if (tid + 1 < nc)
+        S.A[tid] = gap;
+    __syncthreads();
+    // 3. the table, one sorted column per thread: T[t][col k] is the max of
+    //    A[t..k-1] for t <= k and of A[k..t-2] for t > k (0 when empty).
+    //    The 32 columns a warp writes at once are distinct, so the stores
+    //    spread over the banks.
+    if (tid < nc) {
+        const u32 k = tid, ck = S.col[k];
         u32 cur = 0;
-        for (u32 k = t; k < nc; ++k) {
-            if (k > t) {
-                u32 a = S.A[k - 1];
-                cur = cur > a ? cur : a;
-            }
-            S.T[t][S.col[k]] = cur;
+        for (u32 t = k + 1; t-- > 0;) {
+            if (t < k)
+                cur = max(cur, S.A[t]);
+            S.T[t][ck] = cur;
         }
         cur = 0;
-        for (u32 k = t; k-- > 0;) {
-            if (k + 1 < t) {
-                u32 a = S.A[k];
-                cur = cur > a ? cur : a;
-            }
-            S.T[t][S.col[k]] = cur;
+        for (u32 t = k + 1; t <= nc; ++t) {
+            if (t >= k + 2)
+                cur = max(cur, S.A[t - 2]);
+            S.T[t][ck] = cur;
         }
     }
-    __syncthreads();
-    // 4. rows: one warp per row, each lane four consecutive columns
     const u32 lane = tid & 31, w = tid >> 5;
     const bool vec = (nc == FC) && (n % 4u) == 0 && (((uintptr_t)M & 15u) == 0);
-    if (vec) {
-        const u32 jj = 4 * lane;
-        const uint4 rk = *reinterpret_cast<const uint4*>(&S.rank[jj]);
-        for (u32 r = w; r < nr; r += nthr / 32) {
-            const u32 t = s_t[r], L = s_L[r], R = s_R[r];
-            const uint4 tv = *reinterpret_cast<const uint4*>(&S.T[t][jj]);
-            u32 v0 = max(tv.x, rk.x >= t ? R : L);
-            u32 v1 = max(tv.y, rk.y >= t ? R : L);
-            u32 v2 = max(tv.z, rk.z >= t ? R : L);
-            u32 v3 = max(tv.w, rk.w >= t ? R : L);
-            uint4 o = make_uint4(bits_of(v0, DT), bits_of(v1, DT), bits_of(v2, DT), bits_of(v3, DT));
-            const u32 i = r0 + r;
-            const u32 dc = i - j0 - jj;     // the diagonal cell is all-zero bits
-            if (dc < 4u) {
-                if (dc == 0) o.x = 0u;
-                if (dc == 1) o.y = 0u;
-                if (dc == 2) o.z = 0u;
-                if (dc == 3) o.w = 0u;
+    for (u32 rb = 0; rb < nr; rb += rows_cap) {
+        const u32 nb = min(rows_cap, nr - rb);
+        // row split points and sides
+        for (u32 r = tid; r < nb; r += nthr) {
+            const u32 p = __ldg(pos + r0 + rb + r);
+            u32 lo = 0, hi = nc;
+            while (lo < hi) {
+                const u32 mid = (lo + hi) >> 1;
+                if (S.q[mid] < p)
+                    lo = mid + 1;
+                else
+                    hi = mid;
             }
-            __stcs(reinterpret_cast<uint4*>(M + (size_t)i * n + j0 + jj), o);
+            s_t[r] = lo;
+            s_L[r] = lo > 0 ? rmq_gap(st, n, S.q[lo - 1], p - 1) : 0u;
+            s_R[r] = (lo < nc && S.q[lo] != p) ? rmq_gap(st, n, p, S.q[lo] - 1) : 0u;
         }
-    } else {
-        for (u32 r = w; r < nr; r += nthr / 32) {
-            const u32 t = s_t[r], L = s_L[r], R = s_R[r];
-            const u32 i = r0 + r;
-            for (u32 c = lane; c < nc; c += 32) {
-                u32 v = max(S.T[t][c], S.rank[c] >= t ? R : L);
-                M[(size_t)i * n + j0 + c] = (j0 + c == i) ? 0u : bits_of(v, DT);
+        __syncthreads();
+        // 4. rows: one warp per row, each lane four consecutive columns
+        if (vec) {
+            const u32 jj = 4 * lane;
+            const uint4 rk = *reinterpret_cast<const uint4*>(&S.rank[jj]);
+            for (u32 r = w; r < nb; r += nthr / 32) {
+                const u32 t = s_t[r], L = s_L[r], R = s_R[r];
+                const uint4 tv = *reinterpret_cast<const uint4*>(&S.T[t][jj]);
+                u32 v0 = max(tv.x, rk.x >= t ? R : L);
+                u32 v1 = max(tv.y, rk.y >= t ? R : L);
+                u32 v2 = max(tv.z, rk.z >= t ? R : L);
+                u32 v3 = max(tv.w, rk.w >= t ? R : L);
+                uint4 o = make_uint4(bits_of(v0, DT), bits_of(v1, DT), bits_of(v2, DT), bits_of(v3, DT));
+                const u32 i = r0 + rb + r;
+                const u32 dc = i - j0 - jj;     // the diagonal cell is all-zero bits
+                if (dc < 4u) {
+                    if (dc == 0) o.x = 0u;
+                    if (dc == 1) o.y = 0u;
+                    if (dc == 2) o.z = 0u;
+                    if (dc == 3) o.w = 0u;
+                }
+                __stcs(reinterpret_cast<uint4*>(M + (size_t)i * n + j0 + jj), o);
+            }
+        } else {
+            for (u32 r = w; r < nb; r += nthr / 32) {
+                const u32 t = s_t[r], L = s_L[r], R = s_R[r];
+                const u32 i = r0 + rb + r;
+                for (u32 c = lane; c < nc; c += 32) {
+                    u32 v = max(S.T[t][c], S.rank[c] >= t ? R : L);
+                    __stcs(M + (size_t)i * n + j0 + c, (j0 + c == i) ? 0u : bits_of(v, DT));
+                }
             }
         }
+        __syncthreads();   // the next batch (or tile) reuses the shared memory
     }
-    __syncthreads();   // the next tile reuses the shared memory
 }
 
 }  // namespace appd

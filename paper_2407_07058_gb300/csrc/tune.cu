@@ -1,9 +1,9 @@
 // tune.cu -- autotuner of the batched path.
 //
 // The batched path has two shape parameters that depend on the GPU: the rows
-// per fill tile inside a CTA (shared memory per CTA vs. the number of tile
-// set-ups per graph) and the size cut-over between one-CTA-per-graph solving
-// and the multi-CTA pipeline.  appd_batched_autotune times every candidate
+// per fill batch inside a CTA (shared memory per CTA vs. the number of row
+// batches per column block) and the size cut-over between one-CTA-per-graph
+// solving and the multi-CTA pipeline.  appd_batched_autotune times every candidate
 // pair on a seeded synthetic batch (graph sizes log-uniform in [32, 4096],
 // uniform(0,1) weights written by a hash kernel below), keeps the fastest,
 // installs it for this process, and caches it in a small JSON file keyed by
@@ -141,7 +141,7 @@ extern "C" appd_status appd_batched_autotune(const char* cache_path, appd_stream
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int rows[] = {64, 128, 256, 512};
+    const int rows[] = {256, 512, 1024, 2048};
     const int64_t splits[] = {512, 1024, 2048, 4096};
     double best_ms = 1e30;
     appd_status st = APPD_OK;

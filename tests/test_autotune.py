@@ -20,7 +20,7 @@ def test_autotune_installs_caches_and_stays_exact(tmp_path):
     try:
         t = appd.batched_autotune(str(cache))
         assert t["ctas_per_sm"] == 1
-        assert t["fill_rows"] in (64, 128, 256, 512)
+        assert t["fill_rows"] in (256, 512, 1024, 2048)
         assert t["n_split"] in (512, 1024, 2048, 4096)
         lines = cache.read_text().splitlines()
         assert len(lines) == 1

@@ -221,7 +221,7 @@ def test_batched_repeat_replays_and_tuning():
     Ws, offs, flat = _batch(sizes, [0] * len(sizes), seed0=1000)
     T = torch.from_numpy(flat.view(np.int32)).cuda()
     refs = [oracle.appd(W) for W in Ws[:25]]
-    for tuning in [(1, 256, 2048), (1, 128, 512), (1, 64, 2048), (1, 512, 100)]:
+    for tuning in [(1, 256, 2048), (1, 128, 512), (1, 64, 2048), (1, 512, 100), (1, 2048, 4096)]:
         appd.batched_tuning(*tuning)
         for _ in range(2):   # second call replays the captured launch
             M = appd.solve_batched(T, offs, sizes)
