@@ -13,7 +13,8 @@ namespace appd {
 
 constexpr int MAX_LEVELS = 20;     // Boruvka levels: ceil(log2 65536) = 16, plus slack
 constexpr int CONTRACT_ROWS = 8;   // rows of the current matrix per contraction work item
-constexpr int CONTRACT_THREADS = 1024;
+constexpr int CONTRACT_THREADS = 1024;   // one contraction CTA per SM
+constexpr int CONTRACT_THREADS2 = 512;   // two per SM (half the bins each)
 
 // Device-resident control block of one solve.
 struct Counters {
@@ -41,7 +42,8 @@ struct Workspace {
     int coop_blocks = 0;     // CTAs of the cooperative kernels
     int coop_threads = 0;
     int contract_blocks = 0;
-    u32 bin_cap = 0;         // u64 bins per contraction CTA
+    u32 bin_cap = 0;         // u64 bins per contraction CTA (one CTA per SM)
+    u32 bin_cap2 = 0;        // u64 bins per contraction CTA (two CTAs per SM)
     void* base = nullptr;
     size_t bytes = 0;
 

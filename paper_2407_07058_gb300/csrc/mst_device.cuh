@@ -176,6 +176,12 @@ __device__ __forceinline__ u32 lane_of(const uint4& v)
     return C == 0 ? v.x : (C == 1 ? v.y : (C == 2 ? v.z : v.w));
 }
 
+// the same with an index that is a compile-time constant after unrolling
+__device__ __forceinline__ u32 lane_of_dyn(const uint4& v, int c)
+{
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
 // one column: the smallest key over the item's rows (first strictly smaller
 // wins, rows ascending), packed with its endpoints, folded into bin L
 template <int DT, int NR, int C>
@@ -292,6 +298,68 @@ __device__ __forceinline__ void contract_cols_w(const u32* __restrict__ Wp, u32 
     }
 }
 
+// Column work of one item pass over the upper triangle of W only (level 0,
+// W symmetric, 16-byte aligned rows): row q contributes its columns j >
+// rows[q].  rows[] is ascending, so columns j <= rows[0] are skipped, row 0
+// is valid wherever any row is (it seeds each column's minimum), and a
+// row's column groups that lie wholly at or left of its diagonal are not
+// loaded.  The result P(A, B) covers pairs a < b only; the symmetric
+// C_1(A, B) = min(P(A, B), P(B, A)) is formed afterwards (k_sym_c1).
+template <int DT>
+__device__ __forceinline__ void contract_cols_w_upper(const u32* __restrict__ Wp, u32 cr,
+                                                      const u32* __restrict__ label,
+                                                      const u32* __restrict__ srows, u32 np, u32 A,
+                                                      u32 b0, u32 nb, u64* bins)
+{
+    constexpr int NR = 4;
+    const u32 tid = threadIdx.x, bd = blockDim.x;
+    u32 rid[NR];
+    const u32* rp[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        rid[q] = srows[(u32)q < np ? q : 0];
+        rp[q] = Wp + (size_t)rid[q] * cr;
+    }
+    const u32 n4 = cr >> 2;
+    for (u32 g = ((rid[0] + 1) >> 2) + tid; g < n4; g += bd) {
+        const u32 j = 4 * g;
+        uint4 v[NR];
+        v[0] = ld_stream_v4(rp[0] + j);
+#pragma unroll
+        for (int q = 1; q < NR; ++q)
+            v[q] = ((u32)q < np && j + 3 > rid[q]) ? ld_stream_v4(rp[q] + j) : v[0];
+        const uint4 lab = *reinterpret_cast<const uint4*>(label + j);
+        const u32 L[4] = {lab.x, lab.y, lab.z, lab.w};
+        u64 e[4];
+        u32 rel[4];
+        bool ok[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const u32 col = j + c;
+            rel[c] = L[c] - b0;
+            ok[c] = (L[c] != A) && (rel[c] < nb) && (col > rid[0]);
+            u32 bk = key_of(lane_of_dyn(v[0], c), DT), bi = rid[0];
+#pragma unroll
+            for (int q = 1; q < NR; ++q) {
+                const u32 k = key_of(lane_of_dyn(v[q], c), DT);
+                if (col > rid[q] && k < bk) {
+                    bk = k;
+                    bi = rid[q];
+                }
+            }
+            e[c] = pack_edge(bk, bi, col);
+        }
+        u64 cur[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            cur[c] = ok[c] ? bins[rel[c]] : 0ull;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (ok[c] && e[c] < cur[c])
+                atomicMin(&bins[rel[c]], e[c]);
+    }
+}
+
 // Column work of one item pass of up to 4 rows of C_r (levels >= 1):
 // entries are packed edges already, so a column reduces by a plain minimum.
 __device__ __forceinline__ void contract_cols_c(const u64* __restrict__ Cp, u32 cr,
@@ -351,8 +419,9 @@ __device__ __forceinline__ void contract_cols_c(const u64* __restrict__ Cp, u32 
 
 // One contraction work item: rows of group A (a chunk of at most
 // CONTRACT_ROWS), one bin range.  Every thread of the CTA calls it; bins is
-// the CTA's shared memory (>= min(cn, bin_cap) u64).
-template <int DT, int LEVEL0, bool VEC>
+// the CTA's shared memory (>= min(cn, bin_cap) u64).  UPPER (level 0, VEC):
+// upper-triangle pass; the row minima come from the symmetrization.
+template <int DT, int LEVEL0, bool VEC, bool UPPER = false>
 __device__ __forceinline__ void contract_item(const ContractArgs& a, u32 item, u32 cr, u32 cn,
                                               u32 total_chunks, u64* bins, u32* s_rows, u64* s_red)
 {
@@ -385,7 +454,9 @@ __device__ __forceinline__ void contract_item(const ContractArgs& a, u32 item, u
     // rows in passes of at most 4 (register budget); bins merge passes
     for (u32 p0 = 0; p0 < nrows; p0 += 4) {
         const u32 np = min(4u, nrows - p0);
-        if (LEVEL0)
+        if (LEVEL0 && UPPER)
+            contract_cols_w_upper<DT>((const u32*)a.cin, cr, a.label, s_rows + p0, np, A, b0, nb, bins);
+        else if (LEVEL0)
             contract_cols_w<DT, VEC>((const u32*)a.cin, cr, a.label, s_rows + p0, np, A, b0, nb, bins);
         else
             contract_cols_c((const u64*)a.cin, cr, a.label, s_rows + p0, np, A, b0, nb, bins);
@@ -402,9 +473,11 @@ __device__ __forceinline__ void contract_item(const ContractArgs& a, u32 item, u
             atomicMin(dst + b, v);
         m = v < m ? v : m;
     }
-    m = block_min_u64(m, s_red);
-    if (tid == 0 && m != EDGE_INF)
-        atomicMin(&a.best_out[A], m);
+    if (!UPPER) {
+        m = block_min_u64(m, s_red);
+        if (tid == 0 && m != EDGE_INF)
+            atomicMin(&a.best_out[A], m);
+    }
     __syncthreads();
 }
 

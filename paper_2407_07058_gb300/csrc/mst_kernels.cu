@@ -103,12 +103,17 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
     const u32 imax = min(n, i0 + RS_ROWS);
     // does any of this warp's columns need the j > i mask?
     const bool mask = (c0 + 128 * w) <= (imax - 1);
-    u64 cm0 = EDGE_INF, cm1 = EDGE_INF, cm2 = EDGE_INF, cm3 = EDGE_INF;
-    for (u32 pass = 0; pass < RS_ROWS / 32; ++pass) {
+    // Column minima as (key, row) pairs.  Rows are visited in descending
+    // order and a key replaces the minimum when <= it, so the survivor is the
+    // smallest key with the smallest row (the packed-edge order for a fixed
+    // column); starting from key 0xFFFFFFFF the first valid row always enters.
+    u32 ck[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    u32 ci[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    for (int pass = RS_ROWS / 32 - 1; pass >= 0; --pass) {
         const u32 ib = i0 + 32 * pass;
         if (ib >= imax)
-            break;
-        for (u32 r8 = 0; r8 < 32; r8 += 8) {
+            continue;
+        for (int r8 = 24; r8 >= 0; r8 -= 8) {
             // issue eight rows' loads before consuming any (memory-level parallelism)
             uint4 v[8];
 #pragma unroll
@@ -118,28 +123,46 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
                     v[q] = ld_stream_v4(W + (size_t)i * n + j);
             }
 #pragma unroll
-            for (u32 q = 0; q < 8; ++q) {
+            for (int q = 7; q >= 0; --q) {
                 const u32 r = r8 + q, i = ib + r;
-                u64 rp = EDGE_INF;
+                // row i's minimum over this lane's columns, same rule over
+                // descending columns: the smallest key at the smallest column
+                u32 rk = 0xFFFFFFFFu, rj = 0xFFFFFFFFu;
                 if (live && i < imax) {
-                    const u32 k0 = key_of(v[q].x, DT), k1 = key_of(v[q].y, DT);
-                    const u32 k2 = key_of(v[q].z, DT), k3 = key_of(v[q].w, DT);
-                    const u64 e0 = ((u64)k0 << 32) | j, e1 = ((u64)k1 << 32) | (j + 1);
-                    const u64 e2 = ((u64)k2 << 32) | (j + 2), e3 = ((u64)k3 << 32) | (j + 3);
-                    const u64 f0 = ((u64)k0 << 32) | i, f1 = ((u64)k1 << 32) | i;
-                    const u64 f2 = ((u64)k2 << 32) | i, f3 = ((u64)k3 << 32) | i;
-                    const bool ok0 = !mask || j > i, ok1 = !mask || j + 1 > i;
-                    const bool ok2 = !mask || j + 2 > i, ok3 = !mask || j + 3 > i;
-                    if (ok0) { rp = e0 < rp ? e0 : rp; cm0 = f0 < cm0 ? f0 : cm0; }
-                    if (ok1) { rp = e1 < rp ? e1 : rp; cm1 = f1 < cm1 ? f1 : cm1; }
-                    if (ok2) { rp = e2 < rp ? e2 : rp; cm2 = f2 < cm2 ? f2 : cm2; }
-                    if (ok3) { rp = e3 < rp ? e3 : rp; cm3 = f3 < cm3 ? f3 : cm3; }
+                    const u32 k[4] = {key_of(v[q].x, DT), key_of(v[q].y, DT), key_of(v[q].z, DT),
+                                      key_of(v[q].w, DT)};
+                    if (!mask) {
+#pragma unroll
+                        for (int c = 3; c >= 0; --c)
+                            if (k[c] <= rk) {
+                                rk = k[c];
+                                rj = j + c;
+                            }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (k[c] <= ck[c]) {
+                                ck[c] = k[c];
+                                ci[c] = i;
+                            }
+                    } else {
+#pragma unroll
+                        for (int c = 3; c >= 0; --c)
+                            if (j + c > i && k[c] <= rk) {
+                                rk = k[c];
+                                rj = j + c;
+                            }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (j + c > i && k[c] <= ck[c]) {
+                                ck[c] = k[c];
+                                ci[c] = i;
+                            }
+                    }
                 }
                 // warp minimum of (key, column) for row i: smallest key, then the
                 // smallest column among the lanes holding it
-                const u32 rk = (u32)(rp >> 32);
                 const u32 kmin = __reduce_min_sync(0xFFFFFFFFu, rk);
-                const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, rk == kmin ? (u32)rp : 0xFFFFFFFFu);
+                const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, rk == kmin ? rj : 0xFFFFFFFFu);
                 if (lane == r && jmin != 0xFFFFFFFFu)
                     atomicMin(&s_row[32 * pass + r], ((u64)kmin << 32) | jmin);
             }
@@ -147,10 +170,10 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
     }
     // column candidates: edge (i, j) with i the smallest-key row (ties: lower i)
     if (live) {
-        if (cm0 != EDGE_INF) atomicMin(&best[j], pack_edge((u32)(cm0 >> 32), (u32)cm0, j));
-        if (cm1 != EDGE_INF) atomicMin(&best[j + 1], pack_edge((u32)(cm1 >> 32), (u32)cm1, j + 1));
-        if (cm2 != EDGE_INF) atomicMin(&best[j + 2], pack_edge((u32)(cm2 >> 32), (u32)cm2, j + 2));
-        if (cm3 != EDGE_INF) atomicMin(&best[j + 3], pack_edge((u32)(cm3 >> 32), (u32)cm3, j + 3));
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (ci[c] != 0xFFFFFFFFu)
+                atomicMin(&best[j + c], pack_edge(ck[c], ci[c], j + c));
     }
     __syncthreads();
     for (u32 r = threadIdx.x; r < RS_ROWS && i0 + r < n; r += blockDim.x) {
@@ -167,13 +190,17 @@ __global__ void k_step(StepArgs a)
 }
 
 // Work loop of the contraction: each CTA takes items (a group A, a chunk of
-// at most CONTRACT_ROWS of its rows, a range of bins), reduces every column
-// of those rows into shared-memory bins indexed by the column's new
-// component, and writes the bins as row A of C_{r+1} (plain stores when one
-// item covers the group, atomic minima otherwise) together with the row's
-// minimum, the next round's best edge of A.
-template <int DT, int LEVEL0, bool VEC>
-__global__ void __launch_bounds__(CONTRACT_THREADS, 1) k_contract(ContractArgs a)
+// at most CONTRACT_ROWS of its rows, a range of a.bin_cap bins), reduces
+// every column of those rows into shared-memory bins indexed by the column's
+// new component, and writes the bins as row A of C_{r+1} (plain stores when
+// one item covers the group, atomic minima otherwise) together with the
+// row's minimum, the next round's best edge of A.  TWO: 512 threads, two
+// CTAs per SM, so one CTA's barriers and bin traffic overlap the other's
+// loads.  The kernel runs only when run_min <= |C_{r+1}| <= run_max (the
+// host enqueues both forms and the device picks by size).
+template <int DT, int LEVEL0, bool VEC, bool UPPER, bool TWO>
+__global__ void __launch_bounds__(TWO ? CONTRACT_THREADS2 : CONTRACT_THREADS, TWO ? 2 : 1)
+    k_contract(ContractArgs a, u32 run_min, u32 run_max)
 {
     extern __shared__ __align__(16) u64 bins[];
     __shared__ u32 s_item, s_rows[CONTRACT_ROWS];
@@ -184,8 +211,10 @@ __global__ void __launch_bounds__(CONTRACT_THREADS, 1) k_contract(ContractArgs a
     const int r = a.level;
     const u32 cr = ((volatile u32*)ctr->c)[r];       // columns of C_r (and rows)
     const u32 cn = ((volatile u32*)ctr->c)[r + 1];   // size of C_{r+1}
+    if (cn < run_min || cn > run_max)
+        return;
     const u32 total_chunks = *(volatile u32*)&ctr->total_chunks;
-    const u32 nbr = *(volatile u32*)&ctr->nbr;
+    const u32 nbr = (cn + a.bin_cap - 1) / a.bin_cap;
     const u32 total = total_chunks * nbr;
     for (;;) {
         if (threadIdx.x == 0)
@@ -194,7 +223,58 @@ __global__ void __launch_bounds__(CONTRACT_THREADS, 1) k_contract(ContractArgs a
         const u32 item = s_item;
         if (item >= total)
             break;
-        contract_item<DT, LEVEL0, VEC>(a, item, cr, cn, total_chunks, bins, s_rows, s_red);
+        contract_item<DT, LEVEL0, VEC, UPPER>(a, item, cr, cn, total_chunks, bins, s_rows, s_red);
+    }
+}
+
+// After the upper-triangle level-0 contraction, P(A, B) holds the minimum
+// over pairs a in A, b in B with a < b, so C_1(A, B) = min(P(A, B), P(B, A)).
+// Each CTA takes tile pairs (ti <= tj) of SYM_T x SYM_T, writes the minimum
+// to both tiles in place (no other CTA touches them), and folds C_1's row
+// minima -- the next round's best edges -- into best_out with atomic minima.
+constexpr u32 SYM_T = 32;
+
+__global__ void __launch_bounds__(256) k_sym_c1(u64* __restrict__ C, Counters* ctr,
+                                                u64* __restrict__ best_out)
+{
+    __shared__ u64 s_a[SYM_T][SYM_T + 1], s_b[SYM_T][SYM_T + 1];
+    if (*(volatile u32*)&ctr->done)
+        return;
+    const u32 cn = ((volatile u32*)ctr->c)[1];
+    const u32 T = (cn + SYM_T - 1) / SYM_T;
+    const u32 x = threadIdx.x & 31, y0 = threadIdx.x >> 5;
+    for (u32 p = blockIdx.x; p < T * T; p += gridDim.x) {
+        const u32 ti = p / T, tj = p - ti * T;
+        if (ti > tj)
+            continue;
+        const u32 ra = ti * SYM_T, rb = tj * SYM_T;
+#pragma unroll
+        for (u32 k = 0; k < SYM_T / 8; ++k) {
+            const u32 y = y0 + 8 * k;
+            s_a[y][x] = (ra + y < cn && rb + x < cn) ? C[(size_t)(ra + y) * cn + rb + x] : EDGE_INF;
+            s_b[y][x] = (rb + y < cn && ra + x < cn) ? C[(size_t)(rb + y) * cn + ra + x] : EDGE_INF;
+        }
+        __syncthreads();
+#pragma unroll
+        for (u32 k = 0; k < SYM_T / 8; ++k) {
+            const u32 y = y0 + 8 * k;
+            // C_1(ra + y, rb + x) and C_1(rb + y, ra + x)
+            const u64 ma = min(s_a[y][x], s_b[x][y]);
+            const u64 mb = min(s_b[y][x], s_a[x][y]);
+            if (ra + y < cn && rb + x < cn)
+                C[(size_t)(ra + y) * cn + rb + x] = ma;
+            if (rb + y < cn && ra + x < cn)
+                C[(size_t)(rb + y) * cn + ra + x] = mb;
+            const u64 wa = warp_min_u64(ma);
+            if (x == 0 && ra + y < cn && wa != EDGE_INF)
+                atomicMin(&best_out[ra + y], wa);
+            if (ti != tj) {
+                const u64 wb = warp_min_u64(mb);
+                if (x == 0 && rb + y < cn && wb != EDGE_INF)
+                    atomicMin(&best_out[rb + y], wb);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -281,14 +361,16 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
     cb[0] = (u64*)(((uintptr_t)cbuf + 15) & ~(uintptr_t)15);
     cb[1] = (u64*)((char*)cb[0] + ((h * h * sizeof(u64) + 15) & ~(size_t)15));
     (void)cbuf_bytes;
-    const size_t smem = (size_t)ws.bin_cap * sizeof(u64);
-    auto k0 = (dt == 0) ? (vec ? k_contract<0, 1, true> : k_contract<0, 1, false>)
-                        : (vec ? k_contract<1, 1, true> : k_contract<1, 1, false>);
-
-    auto k1 = k_contract<0, 0, false>;
-    if ((err = set_smem(k0, smem)) != cudaSuccess)
-        return err;
-    if ((err = set_smem(k1, smem)) != cudaSuccess)
+    const size_t smem = (size_t)ws.bin_cap * sizeof(u64), smem2 = (size_t)ws.bin_cap2 * sizeof(u64);
+    // level 0 reads the upper triangle of W when rows are 16-byte aligned;
+    // two CTAs per SM when C_1's row fits their bins, else one with all bins
+    auto k0a = (dt == 0) ? (vec ? k_contract<0, 1, true, true, true> : k_contract<0, 1, false, false, true>)
+                         : (vec ? k_contract<1, 1, true, true, true> : k_contract<1, 1, false, false, true>);
+    auto k0b = (dt == 0) ? (vec ? k_contract<0, 1, true, true, false> : k_contract<0, 1, false, false, false>)
+                         : (vec ? k_contract<1, 1, true, true, false> : k_contract<1, 1, false, false, false>);
+    auto k1 = k_contract<0, 0, false, false, true>;
+    if ((err = set_smem(k0a, smem2)) != cudaSuccess || (err = set_smem(k0b, smem)) != cudaSuccess ||
+        (err = set_smem(k1, smem2)) != cudaSuccess)
         return err;
     for (int r = 0; r < ws.levels; ++r) {
         StepArgs sa;
@@ -340,13 +422,21 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         ca.item_group = ws.item_group;
         ca.ctr = ws.ctr;
         ca.bin_cap = ws.bin_cap;
-        dim3 grid(ws.contract_blocks), block(CONTRACT_THREADS);
         const int ph = (r == 0) ? PH_CONTRACT0 : PH_CONTRACT;
         prof_begin(ph, s);
-        if (r == 0)
-            k0<<<grid, block, smem, s>>>(ca);
-        else
-            k1<<<grid, block, smem, s>>>(ca);
+        ContractArgs ca1 = ca;
+        ca.bin_cap = ws.bin_cap2;
+        if (r == 0) {
+            k0a<<<2 * ws.contract_blocks, CONTRACT_THREADS2, smem2, s>>>(ca, 0u, ws.bin_cap2);
+            k0b<<<ws.contract_blocks, CONTRACT_THREADS, smem, s>>>(ca1, ws.bin_cap2 + 1, 0xFFFFFFFFu);
+            prof_launches(1);
+        } else {
+            k1<<<2 * ws.contract_blocks, CONTRACT_THREADS2, smem2, s>>>(ca, 0u, 0xFFFFFFFFu);
+        }
+        if (r == 0 && vec) {
+            prof_launches(1);
+            k_sym_c1<<<ws.sms * 8, 256, 0, s>>>(cb[0], ws.ctr, ws.best[1]);
+        }
         prof_end(ph, s);
         if ((err = cudaGetLastError()) != cudaSuccess)
             return err;
