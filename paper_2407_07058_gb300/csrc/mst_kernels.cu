@@ -232,32 +232,42 @@ __global__ void __launch_bounds__(TWO ? CONTRACT_THREADS2 : CONTRACT_THREADS, TW
 // Each CTA takes tile pairs (ti <= tj) of SYM_T x SYM_T, writes the minimum
 // to both tiles in place (no other CTA touches them), and folds C_1's row
 // minima -- the next round's best edges -- into best_out with atomic minima.
-constexpr u32 SYM_T = 32;
+constexpr u32 SYM_T = 64, SYM_THREADS = 512;
 
-__global__ void __launch_bounds__(256) k_sym_c1(u64* __restrict__ C, Counters* ctr,
-                                                u64* __restrict__ best_out)
+__global__ void __launch_bounds__(SYM_THREADS) k_sym_c1(u64* __restrict__ C, Counters* ctr,
+                                                        u64* __restrict__ best_out)
 {
-    __shared__ u64 s_a[SYM_T][SYM_T + 1], s_b[SYM_T][SYM_T + 1];
+    extern __shared__ __align__(16) u64 s_sym[];
+    u64(*s_a)[SYM_T + 1] = reinterpret_cast<u64(*)[SYM_T + 1]>(s_sym);
+    u64(*s_b)[SYM_T + 1] = reinterpret_cast<u64(*)[SYM_T + 1]>(s_sym + SYM_T * (SYM_T + 1));
     if (*(volatile u32*)&ctr->done)
         return;
     const u32 cn = ((volatile u32*)ctr->c)[1];
     const u32 T = (cn + SYM_T - 1) / SYM_T;
-    const u32 x = threadIdx.x & 31, y0 = threadIdx.x >> 5;
+    constexpr u32 RY = SYM_THREADS / SYM_T;   // rows per sweep
+    const u32 x = threadIdx.x % SYM_T, y0 = threadIdx.x / SYM_T;
     for (u32 p = blockIdx.x; p < T * T; p += gridDim.x) {
         const u32 ti = p / T, tj = p - ti * T;
         if (ti > tj)
             continue;
         const u32 ra = ti * SYM_T, rb = tj * SYM_T;
+        // all sixteen loads of a thread are issued before any is used
+        u64 va[SYM_T / RY], vb[SYM_T / RY];
 #pragma unroll
-        for (u32 k = 0; k < SYM_T / 8; ++k) {
-            const u32 y = y0 + 8 * k;
-            s_a[y][x] = (ra + y < cn && rb + x < cn) ? C[(size_t)(ra + y) * cn + rb + x] : EDGE_INF;
-            s_b[y][x] = (rb + y < cn && ra + x < cn) ? C[(size_t)(rb + y) * cn + ra + x] : EDGE_INF;
+        for (u32 k = 0; k < SYM_T / RY; ++k) {
+            const u32 y = y0 + RY * k;
+            va[k] = (ra + y < cn && rb + x < cn) ? C[(size_t)(ra + y) * cn + rb + x] : EDGE_INF;
+            vb[k] = (rb + y < cn && ra + x < cn) ? C[(size_t)(rb + y) * cn + ra + x] : EDGE_INF;
+        }
+#pragma unroll
+        for (u32 k = 0; k < SYM_T / RY; ++k) {
+            s_a[y0 + RY * k][x] = va[k];
+            s_b[y0 + RY * k][x] = vb[k];
         }
         __syncthreads();
 #pragma unroll
-        for (u32 k = 0; k < SYM_T / 8; ++k) {
-            const u32 y = y0 + 8 * k;
+        for (u32 k = 0; k < SYM_T / RY; ++k) {
+            const u32 y = y0 + RY * k;
             // C_1(ra + y, rb + x) and C_1(rb + y, ra + x)
             const u64 ma = min(s_a[y][x], s_b[x][y]);
             const u64 mb = min(s_b[y][x], s_a[x][y]);
@@ -266,17 +276,19 @@ __global__ void __launch_bounds__(256) k_sym_c1(u64* __restrict__ C, Counters* c
             if (rb + y < cn && ra + x < cn)
                 C[(size_t)(rb + y) * cn + ra + x] = mb;
             const u64 wa = warp_min_u64(ma);
-            if (x == 0 && ra + y < cn && wa != EDGE_INF)
+            if ((threadIdx.x & 31) == 0 && ra + y < cn && wa != EDGE_INF)
                 atomicMin(&best_out[ra + y], wa);
             if (ti != tj) {
                 const u64 wb = warp_min_u64(mb);
-                if (x == 0 && rb + y < cn && wb != EDGE_INF)
+                if ((threadIdx.x & 31) == 0 && rb + y < cn && wb != EDGE_INF)
                     atomicMin(&best_out[rb + y], wb);
             }
         }
         __syncthreads();
     }
 }
+
+inline size_t sym_smem_bytes() { return 2 * SYM_T * (SYM_T + 1) * sizeof(u64); }
 
 // ------------------------------------------------------------------ host
 namespace {
@@ -370,7 +382,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
                          : (vec ? k_contract<1, 1, true, true, false> : k_contract<1, 1, false, false, false>);
     auto k1 = k_contract<0, 0, false, false, true>;
     if ((err = set_smem(k0a, smem2)) != cudaSuccess || (err = set_smem(k0b, smem)) != cudaSuccess ||
-        (err = set_smem(k1, smem2)) != cudaSuccess)
+        (err = set_smem(k1, smem2)) != cudaSuccess || (err = set_smem(k_sym_c1, sym_smem_bytes())) != cudaSuccess)
         return err;
     for (int r = 0; r < ws.levels; ++r) {
         StepArgs sa;
@@ -435,7 +447,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         }
         if (r == 0 && vec) {
             prof_launches(1);
-            k_sym_c1<<<ws.sms * 8, 256, 0, s>>>(cb[0], ws.ctr, ws.best[1]);
+            k_sym_c1<<<ws.sms * 3, SYM_THREADS, sym_smem_bytes(), s>>>(cb[0], ws.ctr, ws.best[1]);
         }
         prof_end(ph, s);
         if ((err = cudaGetLastError()) != cudaSuccess)
