@@ -13,6 +13,11 @@ return the matrix of original weight bits in the same dtype (diagonal 0):
 - ``brute(W)``: all simple paths, Eq. 1-2, n <= 9.
 - ``prim(W)``: Prim order and the MST edge codes.
 - ``tree_rows(W, mst, sources)``: rows of M by traversing the MST.
+
+Every function takes ``widest=True`` for the widest-path matrix (Section 4.2:
+the largest possible smallest edge weight over all paths), computed by the
+same routines with the order of every comparison reversed -- a maximum
+spanning tree, its edges removed in ascending order.
 """
 from __future__ import annotations
 
@@ -29,6 +34,7 @@ _LOCK = threading.Lock()
 _LIB = None
 
 F32, U32 = 0, 1
+WIDEST = 2   # flag: reverse the order (widest paths)
 
 
 def build() -> str:
@@ -63,7 +69,7 @@ def _lib():
     return _LIB
 
 
-def _prep(W: np.ndarray):
+def _prep(W: np.ndarray, widest: bool = False):
     if W.dtype == np.float32:
         dt = F32
     elif W.dtype == np.uint32:
@@ -73,7 +79,7 @@ def _prep(W: np.ndarray):
     if W.ndim != 2 or W.shape[0] != W.shape[1]:
         raise ValueError("W must be square")
     Wc = np.ascontiguousarray(W)
-    return Wc, Wc.shape[0], dt
+    return Wc, Wc.shape[0], dt | (WIDEST if widest else 0)
 
 
 def _check(rc: int, what: str):
@@ -81,8 +87,8 @@ def _check(rc: int, what: str):
         raise RuntimeError(f"{what} failed with code {rc}")
 
 
-def appd(W: np.ndarray, *, return_fill_count: bool = False):
-    Wc, n, dt = _prep(W)
+def appd(W: np.ndarray, *, return_fill_count: bool = False, widest: bool = False):
+    Wc, n, dt = _prep(W, widest)
     M = np.empty_like(Wc)
     cnt = ctypes.c_int64(0)
     _check(_lib().appd_oracle_alg4(Wc.ctypes.data, n, dt, M.ctypes.data, ctypes.byref(cnt)),
@@ -90,34 +96,35 @@ def appd(W: np.ndarray, *, return_fill_count: bool = False):
     return (M, cnt.value) if return_fill_count else M
 
 
-def appd_ascending(W: np.ndarray) -> np.ndarray:
-    Wc, n, dt = _prep(W)
+def appd_ascending(W: np.ndarray, widest: bool = False) -> np.ndarray:
+    Wc, n, dt = _prep(W, widest)
     M = np.empty_like(Wc)
     _check(_lib().appd_oracle_ascending(Wc.ctypes.data, n, dt, M.ctypes.data),
            "appd_oracle_ascending")
     return M
 
 
-def fw(W: np.ndarray) -> np.ndarray:
-    Wc, n, dt = _prep(W)
+def fw(W: np.ndarray, widest: bool = False) -> np.ndarray:
+    Wc, n, dt = _prep(W, widest)
     M = np.empty_like(Wc)
     _check(_lib().appd_oracle_fw(Wc.ctypes.data, n, dt, M.ctypes.data), "appd_oracle_fw")
     return M
 
 
-def brute(W: np.ndarray) -> np.ndarray:
-    Wc, n, dt = _prep(W)
+def brute(W: np.ndarray, widest: bool = False) -> np.ndarray:
+    Wc, n, dt = _prep(W, widest)
     M = np.empty_like(Wc)
     _check(_lib().appd_oracle_brute(Wc.ctypes.data, n, dt, M.ctypes.data), "appd_oracle_brute")
     return M
 
 
-def prim(W: np.ndarray):
+def prim(W: np.ndarray, widest: bool = False):
     """Return (order, mst_codes): Prim order from vertex 0 and the n-1 edge codes.
 
-    mst_codes[k] = key << 32 | lo << 16 | hi of the edge that added order[k+1].
+    mst_codes[k] = key << 32 | lo << 16 | hi of the edge that added order[k+1]
+    (with widest=True: the maximum spanning tree, key complemented).
     """
-    Wc, n, dt = _prep(W)
+    Wc, n, dt = _prep(W, widest)
     order = np.empty(n, dtype=np.uint32)
     mst = np.empty(max(n - 1, 1), dtype=np.uint64)
     _check(_lib().appd_oracle_prim(Wc.ctypes.data, n, dt, mst.ctypes.data, order.ctypes.data),
@@ -125,8 +132,8 @@ def prim(W: np.ndarray):
     return order, mst[: n - 1]
 
 
-def tree_rows(W: np.ndarray, mst: np.ndarray, sources) -> np.ndarray:
-    Wc, n, dt = _prep(W)
+def tree_rows(W: np.ndarray, mst: np.ndarray, sources, widest: bool = False) -> np.ndarray:
+    Wc, n, dt = _prep(W, widest)
     src = np.ascontiguousarray(np.asarray(sources, dtype=np.uint32))
     mst = np.ascontiguousarray(mst, dtype=np.uint64)
     rows = np.empty((len(src), n), dtype=Wc.dtype)

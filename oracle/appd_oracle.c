@@ -27,6 +27,15 @@
  *  - W must be symmetric (an undirected graph, Section 1); only the upper
  *    triangle W(i,j), i<j, is read as the weight of edge {i,j}.
  *
+ * Widest paths (Section 4.2): the widest-path distance is the largest
+ * possible smallest edge weight over all i-j paths.  The paper solves it with
+ * the same Algorithm 4 on a maximum spanning tree whose edges are removed in
+ * ascending order.  Here a dtype with bit 1 set (OR_WIDEST) reverses the
+ * order of every comparison: the key of a weight is complemented, so Prim's
+ * "smallest next edge" builds the maximum spanning tree, the descending
+ * removal runs from the smallest weight up, and every routine below computes
+ * the widest-path matrix.  The output cells still hold original bits.
+ *
  * Test-only routines in this file: the ascending (small-to-large) form of
  * Section 3, the (min,max) Floyd-Warshall variant named in Section 1 and
  * Table 1, brute-force enumeration of simple paths (Eq. 1-2 written out),
@@ -41,20 +50,25 @@
 
 #define OR_F32 0
 #define OR_U32 1
+#define OR_WIDEST 2   /* flag: reverse the order (widest paths, Section 4.2) */
 
 static int g_mutation = 0;
 
 void appd_oracle_set_mutation(int m) { g_mutation = m; }
 int appd_oracle_get_mutation(void) { return g_mutation; }
 
-/* Order key of one weight: unsigned compare on the key == IEEE totalOrder. */
+/* Order key of one weight: unsigned compare on the key == IEEE totalOrder
+ * (or the reverse of it, with the widest flag). */
 static uint32_t order_key(uint32_t bits, int dtype)
 {
-    if (dtype == OR_U32)
-        return bits;
-    if (bits & 0x80000000u)
-        return ~bits;            /* negative: larger magnitude sorts lower */
-    return bits | 0x80000000u;   /* non-negative: above every negative */
+    uint32_t k;
+    if (dtype & OR_U32)
+        k = bits;
+    else if (bits & 0x80000000u)
+        k = ~bits;               /* negative: larger magnitude sorts lower */
+    else
+        k = bits | 0x80000000u;  /* non-negative: above every negative */
+    return (dtype & OR_WIDEST) ? ~k : k;
 }
 
 static uint32_t w_bits(const uint32_t *W, int64_t n, int64_t i, int64_t j)
