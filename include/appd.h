@@ -21,6 +21,13 @@
  *    (the largest edge on a minimax path); the diagonal M(i,i) is all-zero
  *    bits.  W(i,i) is never read.  Results are exact (bit-identical to the
  *    definition), so there is no tolerance.
+ *  - Widest paths (Section 4.2): the dtypes APPD_F32_WIDEST / APPD_U32_WIDEST
+ *    (the base dtype with the APPD_WIDEST bit set) compute instead the
+ *    widest-path matrix, M(i,j) = max over all i-j paths p of the smallest
+ *    edge weight on p (maximum capacity / bottleneck paths).  Every
+ *    comparison runs in the reversed order, so the MST becomes the maximum
+ *    spanning tree; the same conventions hold otherwise (original bits out,
+ *    all-zero diagonal).  Every entry point that takes a dtype accepts them.
  *  - W must be symmetric (undirected graph, Section 1).  Only the upper
  *    triangle is relied on by the specification; results for an asymmetric W
  *    are unspecified.  appd_check_symmetric validates.
@@ -54,7 +61,15 @@ extern "C" {
  * does not require the CUDA headers. */
 typedef struct CUstream_st *appd_stream_t;
 
-typedef enum { APPD_F32 = 0, APPD_U32 = 1 } appd_dtype;
+typedef enum {
+    APPD_F32 = 0,
+    APPD_U32 = 1,
+    APPD_F32_WIDEST = 2,   /* APPD_F32 | APPD_WIDEST */
+    APPD_U32_WIDEST = 3    /* APPD_U32 | APPD_WIDEST */
+} appd_dtype;
+
+/* dtype bit that selects the widest-path matrix (Section 4.2) */
+#define APPD_WIDEST 2
 
 typedef enum {
     APPD_OK = 0,
@@ -130,8 +145,9 @@ appd_status appd_solve_noalloc(const void *W, int64_t n, appd_dtype dt, void *M,
  *   edges_out  device pointer to n-1 uint64 values; each is
  *              key << 32 | lo << 16 | hi, where lo < hi are the endpoints and
  *              key is the order key of W(lo,hi) (the weight's bits for U32;
- *              for F32, bits | 0x80000000 if the sign bit is clear, else ~bits).
- *              Edge order in the array is unspecified.
+ *              for F32, bits | 0x80000000 if the sign bit is clear, else ~bits;
+ *              complemented for the widest dtypes, whose tree is the maximum
+ *              spanning tree).  Edge order in the array is unspecified.
  * Under the strict order (key, lo, hi) the MST is unique, so the edge set can
  * be compared exactly with any correct MST algorithm (Section 3 uses Prim).
  */

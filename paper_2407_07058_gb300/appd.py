@@ -17,6 +17,8 @@ import numpy as np
 from . import _build
 
 F32, U32 = 0, 1
+WIDEST = 2                       # dtype bit: widest paths (Section 4.2)
+F32_WIDEST, U32_WIDEST = 2, 3
 STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD_ERR_NOMEM",
           4: "APPD_ERR_CUDA", 5: "APPD_ERR_ASYMMETRIC", 6: "APPD_ERR_TIMEOUT", 7: "APPD_ERR_BUSY",
           8: "APPD_ERR_ALIAS", 9: "APPD_ERR_NOT_FOUND", 10: "APPD_ERR_INTERNAL"}
@@ -119,11 +121,13 @@ def _square_cuda(W):
     return W.shape[0]
 
 
-def solve(W, out=None, stream=None, alg4: bool = False):
-    """APPD matrix of W (n x n, symmetric) on W's device; returns M (same dtype)."""
+def solve(W, out=None, stream=None, alg4: bool = False, widest: bool = False):
+    """APPD matrix of W (n x n, symmetric) on W's device; returns M (same dtype).
+
+    widest=True gives the widest-path matrix instead (largest smallest edge)."""
     import torch
     n = _square_cuda(W)
-    dt = _dtype_code(W)
+    dt = _dtype_code(W) | (WIDEST if widest else 0)
     M = torch.empty_like(W) if out is None else out
     fn = load().appd_solve_alg4 if alg4 else load().appd_solve
     with torch.cuda.device(W.device):
@@ -131,11 +135,11 @@ def solve(W, out=None, stream=None, alg4: bool = False):
     return M
 
 
-def solve_alg4(W, out=None, stream=None):
-    return solve(W, out=out, stream=stream, alg4=True)
+def solve_alg4(W, out=None, stream=None, widest: bool = False):
+    return solve(W, out=out, stream=stream, alg4=True, widest=widest)
 
 
-def solve_host(W: np.ndarray, stream=None) -> np.ndarray:
+def solve_host(W: np.ndarray, stream=None, widest: bool = False) -> np.ndarray:
     """APPD of a host matrix through appd_solve_host (copies inside the call)."""
     Wc = np.ascontiguousarray(W)
     if Wc.dtype == np.float32:
@@ -144,6 +148,7 @@ def solve_host(W: np.ndarray, stream=None) -> np.ndarray:
         dt = U32
     else:
         raise TypeError(f"unsupported dtype {Wc.dtype}")
+    dt |= WIDEST if widest else 0
     M = np.empty_like(Wc)
     _check(load().appd_solve_host(Wc.ctypes.data, Wc.shape[0], dt, M.ctypes.data,
                                   _stream_ptr(stream)), "appd_solve_host")
@@ -155,31 +160,35 @@ def solve_host_ptr(W_ptr: int, n: int, dt: int, M_ptr: int, stream=None):
     _check(load().appd_solve_host(W_ptr, n, dt, M_ptr, _stream_ptr(stream)), "appd_solve_host")
 
 
-def mst(W, stream=None):
-    """The n-1 MST edges as int64 values key<<32 | lo<<16 | hi (order unspecified)."""
+def mst(W, stream=None, widest: bool = False):
+    """The n-1 MST edges as int64 values key<<32 | lo<<16 | hi (order unspecified);
+    widest=True: the maximum spanning tree, keys complemented."""
     import torch
     n = _square_cuda(W)
     E = torch.empty(max(n - 1, 1), dtype=torch.int64, device=W.device)
+    dt = _dtype_code(W) | (WIDEST if widest else 0)
     with torch.cuda.device(W.device):
-        _check(load().appd_mst(W.data_ptr(), n, _dtype_code(W), E.data_ptr(), _stream_ptr(stream)),
-               "appd_mst")
+        _check(load().appd_mst(W.data_ptr(), n, dt, E.data_ptr(), _stream_ptr(stream)), "appd_mst")
     return E[: n - 1]
 
 
-def leaf_order(W, stream=None):
+def leaf_order(W, stream=None, widest: bool = False):
     """(pos, gap): leaf position of each vertex and the n-1 merge-height keys."""
     import torch
     n = _square_cuda(W)
     pos = torch.empty(n, dtype=torch.int32, device=W.device)
     gap = torch.empty(max(n - 1, 1), dtype=torch.int32, device=W.device)
+    dt = _dtype_code(W) | (WIDEST if widest else 0)
     with torch.cuda.device(W.device):
-        _check(load().appd_leaf_order(W.data_ptr(), n, _dtype_code(W), pos.data_ptr(),
+        _check(load().appd_leaf_order(W.data_ptr(), n, dt, pos.data_ptr(),
                                       gap.data_ptr(), _stream_ptr(stream)), "appd_leaf_order")
     return pos, gap[: n - 1]
 
 
 def solve_batched(Wflat, offsets, ns, dts=None, out=None, stream=None):
-    """Many graphs: graph g is Wflat[offsets[g] : offsets[g] + ns[g]**2] (row-major)."""
+    """Many graphs: graph g is Wflat[offsets[g] : offsets[g] + ns[g]**2] (row-major).
+
+    dts[g] is F32, U32, F32_WIDEST or U32_WIDEST (None: all F32)."""
     import torch
     if not Wflat.is_cuda:
         raise ValueError("Wflat must be a CUDA tensor")

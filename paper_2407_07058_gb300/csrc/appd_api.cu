@@ -207,7 +207,7 @@ void set_sizes(Workspace& w, int64_t n)
 
 appd_status check_args(const void* W, int64_t n, int dt, const void* M)
 {
-    if (n < 0 || !W || !M || (dt != APPD_F32 && dt != APPD_U32))
+    if (n < 0 || !W || !M || !dtype_ok(dt))
         return APPD_ERR_INVALID;
     if (n > 65536)
         return APPD_ERR_TOO_LARGE;
@@ -524,7 +524,7 @@ appd_status appd_mst(const void* W, int64_t n, appd_dtype dt, uint64_t* edges_ou
 appd_status appd_leaf_order(const void* W, int64_t n, appd_dtype dt, uint32_t* pos_out,
                             uint32_t* gap_out, appd_stream_t s)
 {
-    if (n < 0 || !W || !pos_out || (n > 1 && !gap_out) || ((int)dt != APPD_F32 && (int)dt != APPD_U32))
+    if (n < 0 || !W || !pos_out || (n > 1 && !gap_out) || !dtype_ok((int)dt))
         return APPD_ERR_INVALID;
     if (n > 65536)
         return APPD_ERR_TOO_LARGE;
@@ -560,7 +560,7 @@ appd_status appd_solve_batched(const int64_t* offsets, const void* Ws, const int
             return APPD_ERR_INVALID;
         if (ns[g] > 65536)
             return APPD_ERR_TOO_LARGE;
-        if (dts && dts[g] != APPD_F32 && dts[g] != APPD_U32)
+        if (dts && !dtype_ok(dts[g]))
             return APPD_ERR_INVALID;
     }
     if (Ws != Ms) {
@@ -634,7 +634,7 @@ appd_status appd_batched_tuning(int32_t ctas_per_sm, int32_t fill_rows, int64_t 
 
 appd_status appd_check_symmetric(const void* W, int64_t n, appd_dtype dt, appd_stream_t s)
 {
-    if (n < 0 || !W || ((int)dt != APPD_F32 && (int)dt != APPD_U32))
+    if (n < 0 || !W || !dtype_ok((int)dt))
         return APPD_ERR_INVALID;
     if (n > 65536)
         return APPD_ERR_TOO_LARGE;

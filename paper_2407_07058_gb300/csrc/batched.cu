@@ -482,10 +482,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
         u32* M = b.mp[g];
         if (n == 0)
             continue;
-        if (b.dts[g] == 1)
-            solve_one<1>(w, W, M, n, b, smem, s_rows, s_red);
-        else
-            solve_one<0>(w, W, M, n, b, smem, s_rows, s_red);
+        switch (b.dts[g]) {
+        case 1: solve_one<1>(w, W, M, n, b, smem, s_rows, s_red); break;
+        case 2: solve_one<2>(w, W, M, n, b, smem, s_rows, s_red); break;
+        case 3: solve_one<3>(w, W, M, n, b, smem, s_rows, s_red); break;
+        default: solve_one<0>(w, W, M, n, b, smem, s_rows, s_red); break;
+        }
     }
 }
 

@@ -28,16 +28,23 @@ constexpr u32 DEV_INTERNAL = 2u;
 // A bounded grid barrier gives up after this long (ns) and reports a timeout.
 constexpr u64 BARRIER_TIMEOUT_NS = 2000000000ull;
 
+// dtype codes: bit 0 = uint32 (else FP32), bit 1 = widest paths (the order
+// is reversed by complementing the key, Section 4.2)
 __host__ __device__ __forceinline__ u32 key_of(u32 bits, int dt)
 {
-    u32 m = (u32)((int)bits >> 31) | 0x80000000u;
-    return dt ? bits : (bits ^ m);
+    const u32 m = (u32)((int)bits >> 31) | 0x80000000u;
+    const u32 k = (dt & 1) ? bits : (bits ^ m);
+    return (dt & 2) ? ~k : k;
 }
 
 __host__ __device__ __forceinline__ u32 bits_of(u32 key, int dt)
 {
-    return dt ? key : (key ^ ((key >> 31) ? 0x80000000u : 0xFFFFFFFFu));
+    const u32 k = (dt & 2) ? ~key : key;
+    return (dt & 1) ? k : (k ^ ((k >> 31) ? 0x80000000u : 0xFFFFFFFFu));
 }
+
+// a valid dtype code (APPD_F32, APPD_U32, either with the widest flag)
+__host__ __device__ __forceinline__ bool dtype_ok(int dt) { return dt >= 0 && dt <= 3; }
 
 __host__ __device__ __forceinline__ u64 pack_edge(u32 key, u32 a, u32 b)
 {

@@ -126,17 +126,11 @@ cudaError_t run_fill(Workspace& ws, int dt, void* M, cudaStream_t s)
     dim3 grid(gx, (n + rows - 1) / rows);
     const size_t smem = fill_smem_bytes(rows);
     cudaError_t e;
-    if (dt == 0) {
-        if ((e = cudaFuncSetAttribute(k_fill<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)fill_smem_bytes(1024))) != cudaSuccess)
-            return e;
-        k_fill<0><<<grid, FT, smem, s>>>(ws.pos, ws.st, n, rows, (u32*)M);
-    } else {
-        if ((e = cudaFuncSetAttribute(k_fill<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)fill_smem_bytes(1024))) != cudaSuccess)
-            return e;
-        k_fill<1><<<grid, FT, smem, s>>>(ws.pos, ws.st, n, rows, (u32*)M);
-    }
+    auto kf = dt == 0 ? k_fill<0> : dt == 1 ? k_fill<1> : dt == 2 ? k_fill<2> : k_fill<3>;
+    if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fill_smem_bytes(1024))) != cudaSuccess)
+        return e;
+    kf<<<grid, FT, smem, s>>>(ws.pos, ws.st, n, rows, (u32*)M);
     return cudaGetLastError();
 }
 
@@ -151,12 +145,9 @@ cudaError_t run_fill_alg4(Workspace& ws, int dt, void* M, u32* status, cudaStrea
     k_a4_scan<<<1, 1024, 0, s>>>(ws.a4_start, m, ws.ctr);
     k_diag_zero<<<(n + 255) / 256, 256, 0, s>>>((u32*)M, n);
     const int grid = ws.sms * 8;
-    if (dt == 0)
-        k_a4_fill<0><<<grid, 256, 0, s>>>(ws.pos, ws.order, ws.nha, ws.nsize, ws.pe_key, ws.a4_start,
-                                         n, ws.ctr, (u32*)M);
-    else
-        k_a4_fill<1><<<grid, 256, 0, s>>>(ws.pos, ws.order, ws.nha, ws.nsize, ws.pe_key, ws.a4_start,
-                                         n, ws.ctr, (u32*)M);
+    auto ka = dt == 0 ? k_a4_fill<0> : dt == 1 ? k_a4_fill<1> : dt == 2 ? k_a4_fill<2> : k_a4_fill<3>;
+    ka<<<grid, 256, 0, s>>>(ws.pos, ws.order, ws.nha, ws.nsize, ws.pe_key, ws.a4_start, n, ws.ctr,
+                            (u32*)M);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@
 // maximum number of rounds and finished rounds exit at once, so a solve is a
 // fixed launch sequence with no host synchronisation.
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "mst_device.cuh"
 
@@ -347,20 +348,20 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         if ((err = cudaMemsetAsync(ws.best[0], 0xFF, (size_t)n * sizeof(u64), s)) != cudaSuccess)
             return err;
         dim3 grid((n + RS_COLS - 1) / RS_COLS, (n + RS_ROWS - 1) / RS_ROWS);
-        if (dt == 0)
-            k_rowmin_sym<0><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
-        else
-            k_rowmin_sym<1><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+        auto kr = dt == 0 ? k_rowmin_sym<0> : dt == 1 ? k_rowmin_sym<1> : dt == 2 ? k_rowmin_sym<2>
+                                                                                : k_rowmin_sym<3>;
+        kr<<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
         if ((err = cudaGetLastError()) != cudaSuccess)
             return err;
     } else {
         int grid = ws.sms * 8;
         if (grid > (int)n)
             grid = (int)n;
-        if (dt == 0)
-            k_rowmin<0, false><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
-        else
-            k_rowmin<1, false><<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+        auto kr = dt == 0   ? k_rowmin<0, false>
+                  : dt == 1 ? k_rowmin<1, false>
+                  : dt == 2 ? k_rowmin<2, false>
+                            : k_rowmin<3, false>;
+        kr<<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
         if ((err = cudaGetLastError()) != cudaSuccess)
             return err;
     }
@@ -376,10 +377,17 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
     const size_t smem = (size_t)ws.bin_cap * sizeof(u64), smem2 = (size_t)ws.bin_cap2 * sizeof(u64);
     // level 0 reads the upper triangle of W when rows are 16-byte aligned;
     // two CTAs per SM when C_1's row fits their bins, else one with all bins
-    auto k0a = (dt == 0) ? (vec ? k_contract<0, 1, true, true, true> : k_contract<0, 1, false, false, true>)
-                         : (vec ? k_contract<1, 1, true, true, true> : k_contract<1, 1, false, false, true>);
-    auto k0b = (dt == 0) ? (vec ? k_contract<0, 1, true, true, false> : k_contract<0, 1, false, false, false>)
-                         : (vec ? k_contract<1, 1, true, true, false> : k_contract<1, 1, false, false, false>);
+    auto pick0 = [&](auto two) {
+        constexpr bool T = decltype(two)::value;
+        switch (dt) {
+        case 0: return vec ? k_contract<0, 1, true, true, T> : k_contract<0, 1, false, false, T>;
+        case 1: return vec ? k_contract<1, 1, true, true, T> : k_contract<1, 1, false, false, T>;
+        case 2: return vec ? k_contract<2, 1, true, true, T> : k_contract<2, 1, false, false, T>;
+        default: return vec ? k_contract<3, 1, true, true, T> : k_contract<3, 1, false, false, T>;
+        }
+    };
+    auto k0a = pick0(std::true_type{});
+    auto k0b = pick0(std::false_type{});
     auto k1 = k_contract<0, 0, false, false, true>;
     if ((err = set_smem(k0a, smem2)) != cudaSuccess || (err = set_smem(k0b, smem)) != cudaSuccess ||
         (err = set_smem(k1, smem2)) != cudaSuccess || (err = set_smem(k_sym_c1, sym_smem_bytes())) != cudaSuccess)

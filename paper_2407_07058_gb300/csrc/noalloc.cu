@@ -210,10 +210,12 @@ __global__ void __launch_bounds__(NOALLOC_THREADS, 1) k_solve_noalloc(NoallocWs 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u32 s_rows[CONTRACT_ROWS];
     __shared__ u64 s_red[32];
-    if (dt == 1)
-        noalloc_solve<1>(w, W, M, n, smem, bin_cap, s_rows, s_red);
-    else
-        noalloc_solve<0>(w, W, M, n, smem, bin_cap, s_rows, s_red);
+    switch (dt) {
+    case 1: noalloc_solve<1>(w, W, M, n, smem, bin_cap, s_rows, s_red); break;
+    case 2: noalloc_solve<2>(w, W, M, n, smem, bin_cap, s_rows, s_red); break;
+    case 3: noalloc_solve<3>(w, W, M, n, smem, bin_cap, s_rows, s_red); break;
+    default: noalloc_solve<0>(w, W, M, n, smem, bin_cap, s_rows, s_red); break;
+    }
 }
 
 namespace {
@@ -304,7 +306,7 @@ using namespace appd;
 extern "C" appd_status appd_solve_noalloc(const void* W, int64_t n, appd_dtype dt, void* M,
                                           appd_stream_t s)
 {
-    if (n < 0 || !W || !M || ((int)dt != APPD_F32 && (int)dt != APPD_U32))
+    if (n < 0 || !W || !M || !dtype_ok((int)dt))
         return APPD_ERR_INVALID;
     if (n > NOALLOC_MAX_N)
         return APPD_ERR_TOO_LARGE;   // the static scratch is sized for NOALLOC_MAX_N vertices

@@ -209,7 +209,7 @@ appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_s
 appd_status appd_server_submit(appd_server* sv, int64_t n, appd_dtype dt, uint64_t* req_id,
                                void** W_slot)
 {
-    if (!sv || !req_id || !W_slot || n <= 0 || ((int)dt != APPD_F32 && (int)dt != APPD_U32))
+    if (!sv || !req_id || !W_slot || n <= 0 || !dtype_ok((int)dt))
         return APPD_ERR_INVALID;
     if (n > 65536)
         return APPD_ERR_TOO_LARGE;
