@@ -298,6 +298,47 @@ __device__ __forceinline__ void contract_cols_w(const u32* __restrict__ Wp, u32 
     }
 }
 
+// One column group (4 columns from j) of an upper-triangle pass: each
+// column's smallest key over the pass's rows (rows ascending, first strictly
+// smaller wins), packed with its endpoints and folded into bin L.  MASK:
+// some row of the pass reaches column j + 3, so each row counts only right
+// of its diagonal; otherwise every row counts at every column.  The chosen
+// row is always left of the column, so (row, column) is already (lo, hi).
+template <int DT, bool MASK>
+__device__ __forceinline__ void fold_upper(const uint4* v, const u32* rid, u32 j, uint4 lab, u32 A,
+                                           u32 b0, u32 nb, u64* bins)
+{
+    constexpr int NR = 4;
+    const u32 L[4] = {lab.x, lab.y, lab.z, lab.w};
+    u64 e[4];
+    u32 rel[4];
+    bool ok[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const u32 col = j + c;
+        rel[c] = L[c] - b0;
+        ok[c] = (L[c] != A) && (rel[c] < nb) && (!MASK || col > rid[0]);
+        u32 bk = key_of(lane_of_dyn(v[0], c), DT), bi = rid[0];
+#pragma unroll
+        for (int q = 1; q < NR; ++q) {
+            const u32 k = key_of(lane_of_dyn(v[q], c), DT);
+            if ((!MASK || col > rid[q]) && k < bk) {
+                bk = k;
+                bi = rid[q];
+            }
+        }
+        e[c] = ((u64)bk << 32) | (bi << 16) | col;
+    }
+    u64 cur[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        cur[c] = ok[c] ? bins[rel[c]] : 0ull;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (ok[c] && e[c] < cur[c])
+            atomicMin(&bins[rel[c]], e[c]);
+}
+
 // Column work of one item pass over the upper triangle of W only (level 0,
 // W symmetric, 16-byte aligned rows): row q contributes its columns j >
 // rows[q].  rows[] is ascending, so columns j <= rows[0] are skipped, row 0
@@ -321,6 +362,7 @@ __device__ __forceinline__ void contract_cols_w_upper(const u32* __restrict__ Wp
         rp[q] = Wp + (size_t)rid[q] * cr;
     }
     const u32 n4 = cr >> 2;
+    const u32 rmax = rid[np - 1];   // the pass's largest row
     for (u32 g = ((rid[0] + 1) >> 2) + tid; g < n4; g += bd) {
         const u32 j = 4 * g;
         uint4 v[NR];
@@ -329,34 +371,10 @@ __device__ __forceinline__ void contract_cols_w_upper(const u32* __restrict__ Wp
         for (int q = 1; q < NR; ++q)
             v[q] = ((u32)q < np && j + 3 > rid[q]) ? ld_stream_v4(rp[q] + j) : v[0];
         const uint4 lab = *reinterpret_cast<const uint4*>(label + j);
-        const u32 L[4] = {lab.x, lab.y, lab.z, lab.w};
-        u64 e[4];
-        u32 rel[4];
-        bool ok[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const u32 col = j + c;
-            rel[c] = L[c] - b0;
-            ok[c] = (L[c] != A) && (rel[c] < nb) && (col > rid[0]);
-            u32 bk = key_of(lane_of_dyn(v[0], c), DT), bi = rid[0];
-#pragma unroll
-            for (int q = 1; q < NR; ++q) {
-                const u32 k = key_of(lane_of_dyn(v[q], c), DT);
-                if (col > rid[q] && k < bk) {
-                    bk = k;
-                    bi = rid[q];
-                }
-            }
-            e[c] = pack_edge(bk, bi, col);
-        }
-        u64 cur[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            cur[c] = ok[c] ? bins[rel[c]] : 0ull;
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (ok[c] && e[c] < cur[c])
-                atomicMin(&bins[rel[c]], e[c]);
+        if (j > rmax)
+            fold_upper<DT, false>(v, rid, j, lab, A, b0, nb, bins);
+        else
+            fold_upper<DT, true>(v, rid, j, lab, A, b0, nb, bins);
     }
 }
 
