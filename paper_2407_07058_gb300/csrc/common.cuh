@@ -151,41 +151,46 @@ __device__ __forceinline__ u32 block_excl_scan(u32 v, u32* total, u32* sh)
 }
 
 // ------------------------------------------------------------ grid barrier
-// Generation barrier for cooperative launches (all CTAs co-resident).  The
-// wait is bounded: after BARRIER_TIMEOUT_NS a CTA records DEV_TIMEOUT and
-// returns false; callers then leave the kernel.  The count and abort words
-// must be zero when the kernel starts (the host clears them before each
-// launch).
+// Counting barrier for cooperative launches (all CTAs co-resident).  Thread 0
+// of each CTA adds one to `count`; the k-th barrier of a launch completes when
+// count reaches k * gridDim.x, so one atomic per CTA and a poll suffice (no
+// reset, no generation word).  The wait is bounded: after BARRIER_TIMEOUT_NS a
+// CTA records DEV_TIMEOUT, sets `abort` and returns false; callers then leave
+// the kernel, and a CTA waiting at any later barrier of the launch sees
+// `abort` and gives up at once.  count and abort must be zero when the kernel
+// starts (the host clears them before each launch).
 struct GridBar {
     u32 count;
-    u32 abort;   // set by the first CTA that gave up; later barriers of the launch fail at once
-    u32 gen;
+    u32 abort;
+    u32 gen;     // unused (layout kept for the host's memset of count + abort)
 };
+
+__device__ __forceinline__ u32 atom_add_release(u32* p, u32 v)
+{
+    u32 old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 
 __device__ __forceinline__ bool grid_sync(GridBar* bar, u32* status,
                                           u64 limit_ns = BARRIER_TIMEOUT_NS)
 {
     __shared__ u32 s_ok;
     __syncthreads();
-    if (threadIdx.x == 0)
-        s_ok = 1;
     if (threadIdx.x == 0) {
         u32 ok = 1;
-        // once any CTA of this launch has given up, every later barrier fails at once
-        if (ld_acquire(&bar->abort)) {
-            s_ok = 0;
-        }
-        u32 g = ld_acquire(&bar->gen);
         __threadfence();
-        u32 arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            u64 t0 = globaltimer_ns();
-            while (s_ok && ld_acquire(&bar->gen) == g) {
-                __nanosleep(40);
+        const u32 nb = gridDim.x;
+        const u32 old = atom_add_release(&bar->count, 1u);
+        const u32 target = (old / nb + 1) * nb;
+        if ((int)(ld_acquire(&bar->count) - target) < 0) {
+            const u64 t0 = globaltimer_ns();
+            while ((int)(ld_acquire(&bar->count) - target) < 0) {
+                if (ld_acquire(&bar->abort)) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
                 if (globaltimer_ns() - t0 > limit_ns) {
                     atomicExch(&bar->abort, 1u);
                     atomicOr(status, DEV_TIMEOUT);
@@ -195,7 +200,7 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, u32* status,
             }
         }
         __threadfence();
-        s_ok = s_ok && ok;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;

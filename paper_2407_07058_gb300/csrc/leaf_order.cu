@@ -20,7 +20,9 @@
 //      (nha, ord); the preorder comes from a second Euler tour.
 //   4. a sparse table over the gaps for O(1) range maxima.
 // All phases run in one cooperative kernel separated by bounded grid
-// barriers.
+// barriers; up to LEAF_BLOCK_MAX_N vertices they run on one CTA instead,
+// whose block barriers cost a fraction of a grid barrier's (the phases are
+// short at that size, so the barriers dominate).
 #include "leaf_device.cuh"
 
 namespace appd {
@@ -28,6 +30,15 @@ namespace appd {
 __global__ void __launch_bounds__(512) k_leaf_order(LeafArgs a)
 {
     GridTeam t{&a.ctr->bar, a.status};
+    leaf_body(t, a);
+}
+
+constexpr u32 LEAF_BLOCK_MAX_N = 2048;
+
+// 512 threads: the radix sort's per-warp counts are sized for 16 warps
+__global__ void __launch_bounds__(512) k_leaf_order_block(LeafArgs a)
+{
+    BlockTeam t;
     leaf_body(t, a);
 }
 
@@ -69,6 +80,10 @@ cudaError_t run_leaf_order(Workspace& ws, u32* status, cudaStream_t s)
     a.part = ws.part;
     a.ctr = ws.ctr;
     a.status = status;
+    if (a.n <= LEAF_BLOCK_MAX_N) {
+        k_leaf_order_block<<<1, 512, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     cudaError_t err = cudaMemsetAsync(&ws.ctr->bar, 0, 2 * sizeof(u32), s);
     if (err != cudaSuccess)
         return err;

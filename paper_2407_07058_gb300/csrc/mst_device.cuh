@@ -20,6 +20,7 @@ struct StepArgs {
     Counters* ctr;
     u32* status;
     u32 bin_cap;
+    u32 update_comp = 1;   // 0: the caller maps comp[] through label[] later
 };
 
 // One Boruvka round's component bookkeeping, written once for a team (the
@@ -104,8 +105,9 @@ __device__ void step_body(const Team& t, const StepArgs& a)
     }
     if (!t.sync())
         return;
-    for (u32 v = me; v < a.n; v += ts)
-        a.comp[v] = a.label[a.comp[v]];
+    if (a.update_comp)
+        for (u32 v = me; v < a.n; v += ts)
+            a.comp[v] = a.label[a.comp[v]];
     for (u32 A = me; A < cn; A += ts) {
         a.nchunk[A] = (a.cnt[A] + CONTRACT_ROWS - 1) / CONTRACT_ROWS;
         a.best_out[A] = EDGE_INF;
@@ -163,6 +165,9 @@ struct ContractArgs {
     const u32 *label, *members, *gstart, *nchunk, *chunk_start, *item_group;
     Counters* ctr;
     u32 bin_cap;
+    u32* comp = nullptr;   // vertex -> component, mapped through label[] here when
+    u32 n = 0;             // this round's step left it (|C_r| <= comp_max_c)
+    u32 comp_max_c = 0;
 };
 
 // Column work of one contraction item with NR rows of W (level 0).  rows[]

@@ -184,9 +184,27 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
     }
 }
 
+// A round's step runs on the cooperative grid while the current matrix has
+// more than STEP_BLOCK_MAX_C rows, else on one CTA, whose barriers cost a
+// fraction of a grid barrier's; the host enqueues both and each form checks
+// the size on the device.  The one-CTA form leaves the O(n) vertex-to-
+// component update to the round's contraction, which runs on the full grid.
+constexpr u32 STEP_BLOCK_MAX_C = 4096, STEP_BLOCK_THREADS = 1024;
+
 __global__ void k_step(StepArgs a)
 {
+    if (((volatile u32*)a.ctr->c)[a.level] <= STEP_BLOCK_MAX_C)
+        return;
     GridTeam t{&a.ctr->bar, a.status};
+    step_body(t, a);
+}
+
+__global__ void __launch_bounds__(STEP_BLOCK_THREADS) k_step_block(StepArgs a)
+{
+    if (((volatile u32*)a.ctr->c)[a.level] > STEP_BLOCK_MAX_C)
+        return;
+    a.update_comp = 0;
+    BlockTeam t;
     step_body(t, a);
 }
 
@@ -214,6 +232,9 @@ __global__ void __launch_bounds__(TWO ? CONTRACT_THREADS2 : CONTRACT_THREADS, TW
     const u32 cn = ((volatile u32*)ctr->c)[r + 1];   // size of C_{r+1}
     if (cn < run_min || cn > run_max)
         return;
+    if (cr <= a.comp_max_c)
+        for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x)
+            a.comp[v] = a.label[a.comp[v]];
     const u32 total_chunks = *(volatile u32*)&ctr->total_chunks;
     const u32 nbr = (cn + a.bin_cap - 1) / a.bin_cap;
     const u32 total = total_chunks * nbr;
@@ -422,10 +443,16 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
             return err;
         void* args[] = {&sa};
         prof_begin(PH_STEP, s);
-        err = cudaLaunchCooperativeKernel((const void*)k_step, dim3(ws.coop_blocks),
-                                          dim3(ws.coop_threads), args, 0, s);
+        // no round can have more rows than n: small graphs skip the grid form
+        err = (n <= STEP_BLOCK_MAX_C) ? cudaSuccess
+                                      : cudaLaunchCooperativeKernel((const void*)k_step, dim3(ws.coop_blocks),
+                                                                    dim3(ws.coop_threads), args, 0, s);
+        if (err == cudaSuccess) {
+            k_step_block<<<1, STEP_BLOCK_THREADS, 0, s>>>(sa);
+            err = cudaGetLastError();
+        }
         prof_end(PH_STEP, s);
-        prof_launches(2);
+        prof_launches(3);
         if (err != cudaSuccess)
             return err;
 
@@ -442,6 +469,9 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         ca.item_group = ws.item_group;
         ca.ctr = ws.ctr;
         ca.bin_cap = ws.bin_cap;
+        ca.comp = ws.comp;
+        ca.n = n;
+        ca.comp_max_c = STEP_BLOCK_MAX_C;
         const int ph = (r == 0) ? PH_CONTRACT0 : PH_CONTRACT;
         prof_begin(ph, s);
         ContractArgs ca1 = ca;
