@@ -54,6 +54,10 @@ struct BatchArgs {
     u32 bin_cap;          // u64 bins that fit the dynamic shared memory
     u32 warp_bins;        // u64 bins per warp when each warp owns a group
     u32 fill_rows;        // rows per fill tile
+    u32* posst;           // leaf positions and sparse tables of all graphs
+    const u64* pst_off;   // graph g's pos at posst + pst_off[g], its table after n entries
+    u64* best0;           // round-1 minima of all graphs (k_rowmin_batched)
+    const u64* row_off;   // graph g's minima at best0 + row_off[g]
 };
 
 constexpr int BATCH_THREADS = 512;
@@ -124,36 +128,83 @@ __device__ __forceinline__ void load_groups(const u32* row, u32 n, const u32* lo
     }
 }
 
-// Round-1 row minima of one graph by one CTA: each warp takes a row and
-// keeps eight 16-byte loads per lane in flight (64 KB per CTA).
+// Round-1 minimum of row i of an n-vertex graph by one warp.  A minimum
+// does not care which lane sees which column, so the warp walks the 16-byte
+// aligned blocks that cover the row (any row alignment, no realignment) and
+// maps each element back to its column; blocks not wholly inside the matrix
+// (only at its two ends) are read element by element.  Minima are kept as
+// (key, column) pairs of 32-bit words: a lane visits its columns in
+// increasing order and keeps the first strictly smaller key (the first
+// valid column always enters), and the warp reduces (key, column).
 template <int DT>
-__device__ void rowmin_cta(const u32* __restrict__ W, u32 n, u64* __restrict__ best)
+__device__ void row_best_warp(const u32* __restrict__ W, u32 n, u32 i, u64* __restrict__ best)
 {
-    constexpr int U = 8;
-    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int U = 4;
+    const u32 lane = threadIdx.x & 31;
     const u32* hi = W + (size_t)n * n;
-    const u32 ng = (n + 3) >> 2;
-    for (u32 i = w; i < n; i += nw) {
-        const u32* r = W + (size_t)i * n;
-        u64 m = EDGE_INF;
-        for (u32 c0 = 0; c0 < ng; c0 += 32 * U) {
-            uint4 v[U];
-            load_groups<U>(r, n, W, hi, c0 + lane, v);
+    const u32* r = W + (size_t)i * n;
+    const u32 s = (u32)(((uintptr_t)r >> 2) & 3u);
+    const u32* base = r - s;
+    const u32 nb = (n + s + 3) >> 2;
+    u32 bk = 0xFFFFFFFFu, bj = 0xFFFFFFFFu;
+    for (u32 b0 = 0; b0 < nb; b0 += 32 * U) {
+        uint4 v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const u32 j = 4 * (c0 + lane + 32 * u);
-                const u32 x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const u64 c = ((u64)key_of(x[t], DT) << 32) | (j + t);
-                    if (j + t < n && j + t != i && c < m)
-                        m = c;
+        for (int u = 0; u < U; ++u) {
+            const u32 bi = b0 + lane + 32 * u;
+            v[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (bi < nb) {
+                const u32* p = base + 4 * (size_t)bi;
+                if (p >= W && p + 4 <= hi) {
+                    v[u] = ld_stream_v4(p);
+                } else {
+                    v[u].x = (p >= W && p < hi) ? ld_stream_u32(p) : 0u;
+                    v[u].y = (p + 1 >= W && p + 1 < hi) ? ld_stream_u32(p + 1) : 0u;
+                    v[u].z = (p + 2 >= W && p + 2 < hi) ? ld_stream_u32(p + 2) : 0u;
+                    v[u].w = (p + 3 >= W && p + 3 < hi) ? ld_stream_u32(p + 3) : 0u;
                 }
             }
         }
-        m = warp_min_u64(m);
-        if (lane == 0)
-            best[i] = pack_edge((u32)(m >> 32), i, (u32)m & 0xFFFFu);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const u32 j0 = 4 * (b0 + lane + 32 * u) - s;   // column of the block's first word (wraps below 0)
+            const u32 x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const u32 j = j0 + t, k = key_of(x[t], DT);
+                if (j < n && j != i && (k < bk || bj == 0xFFFFFFFFu)) {
+                    bk = k;
+                    bj = j;
+                }
+            }
+        }
+    }
+    const u32 kmin = __reduce_min_sync(0xFFFFFFFFu, bj == 0xFFFFFFFFu ? 0xFFFFFFFFu : bk);
+    const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, (bj != 0xFFFFFFFFu && bk == kmin) ? bj : 0xFFFFFFFFu);
+    if (lane == 0)
+        best[i] = pack_edge(kmin, i, jmin);
+}
+
+// Round-1 minima of every graph of a batch before k_batched: one CTA per
+// task of ROWB_ROWS rows of one graph, a warp per row, at full occupancy.
+constexpr int ROWB_THREADS = 256;
+constexpr u32 ROWB_ROWS = 32;
+
+__global__ void __launch_bounds__(ROWB_THREADS) k_rowmin_batched(BatchArgs b, const uint2* __restrict__ tasks)
+{
+    const uint2 tk = tasks[blockIdx.x];   // graph, first row
+    const u32 g = tk.x, n = b.ns[g];
+    const u32* W = b.wp[g];
+    u64* best = b.best0 + b.row_off[g];
+    const u32 w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const u32 r1 = min(n, tk.y + ROWB_ROWS);
+    for (u32 i = tk.y + w; i < r1; i += nw) {
+        switch (b.dts[g]) {
+        case 1: row_best_warp<1>(W, n, i, best); break;
+        case 2: row_best_warp<2>(W, n, i, best); break;
+        case 3: row_best_warp<3>(W, n, i, best); break;
+        default: row_best_warp<0>(W, n, i, best); break;
+        }
     }
 }
 
@@ -310,8 +361,8 @@ __device__ void contract_level_warps(const ContractArgs& a, u32 cr, u32 cn, u32 
 }
 
 template <int DT>
-__device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, const BatchArgs& b,
-                          unsigned char* smem, u32* s_rows, u64* s_red)
+__device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, u32* pos_g, u64* best0,
+                          const BatchArgs& b, unsigned char* smem, u32* s_rows, u64* s_red)
 {
     BlockTeam t;
     const u32 tid = threadIdx.x;
@@ -332,7 +383,7 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, const B
         ctr->mst_count = 0;
         ctr->jump_flag[0] = ctr->jump_flag[1] = ctr->jump_flag[2] = 0;
     }
-    rowmin_cta<DT>(W, n, w.best0);
+    // round-1 minima come from k_rowmin_batched (best0)
     __syncthreads();
     const bool vec = (n % 4 == 0) && (((uintptr_t)W & 15u) == 0);
 
@@ -349,8 +400,8 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, const B
         StepArgs sa;
         sa.level = r;
         sa.n = n;
-        sa.best_in = (r & 1) ? w.best1 : w.best0;
-        sa.best_out = (r & 1) ? w.best0 : w.best1;
+        sa.best_in = (r & 1) ? w.best1 : best0;
+        sa.best_out = (r & 1) ? best0 : w.best1;
         sa.comp = w.comp;
         sa.hook = w.hook;
         sa.par = w.par;
@@ -444,21 +495,19 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, const B
     la.ntiles = (n - 1 + 2047) / 2048;
     la.first_child = w.first_child;
     la.next_sib = w.next_sib;
-    la.pos = w.pos;
+    la.pos = pos_g;
     la.order = w.order;
     la.nsize = w.nsize;
     la.gap = w.gap;
-    la.st = w.st;
+    la.st = pos_g + n;
     la.part = w.part;
     la.ctr = ctr;
     la.status = b.status;
     leaf_body(t, la);
     __syncthreads();
 
-    // one column block at a time, all rows (in batches of fill_rows): the
-    // block's sort and table are built once
-    for (u32 j0 = 0; j0 < n; j0 += FC)
-        fill_tile<DT>(w.pos, w.st, n, j0, 0, n, b.fill_rows, M, smem);
+    // the fill runs afterwards for every graph of the batch at once
+    // (k_fill_batched), reading pos and the sparse table from posst
 }
 
 __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
@@ -482,12 +531,34 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
         u32* M = b.mp[g];
         if (n == 0)
             continue;
+        u32* pos_g = b.posst + b.pst_off[g];
+        u64* best_g = b.best0 + b.row_off[g];
         switch (b.dts[g]) {
-        case 1: solve_one<1>(w, W, M, n, b, smem, s_rows, s_red); break;
-        case 2: solve_one<2>(w, W, M, n, b, smem, s_rows, s_red); break;
-        case 3: solve_one<3>(w, W, M, n, b, smem, s_rows, s_red); break;
-        default: solve_one<0>(w, W, M, n, b, smem, s_rows, s_red); break;
+        case 1: solve_one<1>(w, W, M, n, pos_g, best_g, b, smem, s_rows, s_red); break;
+        case 2: solve_one<2>(w, W, M, n, pos_g, best_g, b, smem, s_rows, s_red); break;
+        case 3: solve_one<3>(w, W, M, n, pos_g, best_g, b, smem, s_rows, s_red); break;
+        default: solve_one<0>(w, W, M, n, pos_g, best_g, b, smem, s_rows, s_red); break;
         }
+    }
+}
+
+// The fill of every graph of a batch: one CTA per tile (graph, 128 columns,
+// up to fill_rows rows), from the tile list built with the batch layout.
+// All CTAs of the GPU share the work, at the occupancy of the single-solve
+// fill, instead of one CTA filling a whole graph.
+constexpr int FILLB_THREADS = 256;
+
+__global__ void __launch_bounds__(FILLB_THREADS) k_fill_batched(BatchArgs b, const uint4* __restrict__ tiles)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint4 tl = tiles[blockIdx.x];   // graph, first column, first row, rows
+    const u32 g = tl.x, n = b.ns[g];
+    const u32* pos = b.posst + b.pst_off[g];
+    switch (b.dts[g]) {
+    case 1: fill_tile<1>(pos, pos + n, n, tl.y, tl.z, tl.w, b.fill_rows, b.mp[g], smem); break;
+    case 2: fill_tile<2>(pos, pos + n, n, tl.y, tl.z, tl.w, b.fill_rows, b.mp[g], smem); break;
+    case 3: fill_tile<3>(pos, pos + n, n, tl.y, tl.z, tl.w, b.fill_rows, b.mp[g], smem); break;
+    default: fill_tile<0>(pos, pos + n, n, tl.y, tl.z, tl.w, b.fill_rows, b.mp[g], smem); break;
     }
 }
 
@@ -505,10 +576,14 @@ struct BatchRuntime {
     void* d_desc = nullptr;        // descriptors of the uncached launch path
     size_t desc_bytes = 0;
     size_t smem = 0;
+    size_t fill_smem = 0;
     u32 bin_cap = 0;
     u32 warp_bins = 0;
+    void* arena = nullptr;         // minima / leaf-order arena of the uncached launch path
+    size_t arena_bytes = 0;
     struct Plan {
         void* dev = nullptr;
+        void* arena = nullptr;
         cudaGraphExec_t exec = nullptr;
     };
     std::map<std::vector<int64_t>, Plan> plans;
@@ -583,38 +658,110 @@ cudaError_t ensure_scratch(BatchRuntime& rt)
     return cudaMemcpy(rt.d_slices, hs.data(), sizeof(SliceWs) * rt.nslices, cudaMemcpyHostToDevice);
 }
 
-// descriptor block layout: wp | mp | ns | queue | dts
-size_t desc_layout(u32 cnt, size_t off[5])
+// descriptor block layout: wp | mp | ns | queue | dts | pst_off | row_off |
+// fill tiles | row tasks
+struct DescLayout {
+    size_t off[9];
+    size_t bytes;
+    u32 ntiles, ntasks;
+    size_t posst_words;   // leaf positions + sparse tables of every graph
+    size_t rows;          // vertices of every graph (round-1 minima)
+    size_t arena_bytes;   // posst, then the minima (8-byte aligned)
+};
+
+// sparse-table levels of an n-vertex graph (as the leaf order builds it)
+inline u32 st_levels_of(u32 n)
 {
-    off[0] = 0;
-    off[1] = off[0] + 8 * (size_t)cnt;
-    off[2] = off[1] + 8 * (size_t)cnt;
-    off[3] = off[2] + 4 * (size_t)cnt;
-    off[4] = off[3] + 4 * (size_t)cnt;
-    return (off[4] + cnt + 255) & ~(size_t)255;
+    u32 l = 1;
+    while (n > 1 && (1u << l) <= n - 1)
+        ++l;
+    return l;
 }
 
-void fill_desc(const BatchDesc& d, std::vector<unsigned char>& host, const size_t off[5])
+DescLayout desc_layout(const BatchDesc& d, u32 fill_rows)
+{
+    DescLayout L;
+    const size_t cnt = d.n.size();
+    L.ntiles = L.ntasks = 0;
+    L.posst_words = L.rows = 0;
+    for (u32 n : d.n) {
+        if (n >= 2) {
+            L.ntiles += ((n + FC - 1) / FC) * ((n + fill_rows - 1) / fill_rows);
+            L.ntasks += (n + ROWB_ROWS - 1) / ROWB_ROWS;
+        }
+        L.posst_words += (size_t)n * (1 + st_levels_of(n));
+        L.rows += n;
+    }
+    auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    L.off[0] = 0;
+    L.off[1] = L.off[0] + 8 * cnt;
+    L.off[2] = L.off[1] + 8 * cnt;
+    L.off[3] = L.off[2] + 4 * cnt;
+    L.off[4] = L.off[3] + 4 * cnt;
+    L.off[5] = a16(L.off[4] + cnt);
+    L.off[6] = a16(L.off[5] + 8 * cnt);
+    L.off[7] = a16(L.off[6] + 8 * cnt);
+    L.off[8] = a16(L.off[7] + 16 * (size_t)L.ntiles);
+    L.bytes = (L.off[8] + 8 * (size_t)L.ntasks + 255) & ~(size_t)255;
+    L.arena_bytes = ((L.posst_words * 4 + 7) & ~(size_t)7) + 8 * L.rows + 256;
+    return L;
+}
+
+void fill_desc(const BatchDesc& d, u32 fill_rows, const DescLayout& L, std::vector<unsigned char>& host)
 {
     const u32 cnt = (u32)d.n.size();
     std::vector<u32> q(cnt);
     std::iota(q.begin(), q.end(), 0u);
     std::stable_sort(q.begin(), q.end(), [&](u32 a, u32 b) { return d.n[a] > d.n[b]; });
-    memcpy(host.data() + off[0], d.w.data(), 8 * cnt);
-    memcpy(host.data() + off[1], d.m.data(), 8 * cnt);
-    memcpy(host.data() + off[2], d.n.data(), 4 * cnt);
-    memcpy(host.data() + off[3], q.data(), 4 * cnt);
-    memcpy(host.data() + off[4], d.dt.data(), cnt);
+    std::vector<u64> pst(cnt), roff(cnt);
+    std::vector<uint4> tiles;
+    std::vector<uint2> tasks;
+    tiles.reserve(L.ntiles);
+    tasks.reserve(L.ntasks);
+    u64 acc = 0, racc = 0;
+    // largest graphs first, so the row tasks and fill tiles of the long
+    // graphs start early
+    for (u32 k = 0; k < cnt; ++k) {
+        const u32 g = q[k];
+        const u32 n = d.n[g];
+        if (n < 2)
+            continue;
+        for (u32 r0 = 0; r0 < n; r0 += ROWB_ROWS)
+            tasks.push_back(make_uint2(g, r0));
+        for (u32 j0 = 0; j0 < n; j0 += FC)
+            for (u32 r0 = 0; r0 < n; r0 += fill_rows)
+                tiles.push_back(make_uint4(g, j0, r0, std::min(fill_rows, n - r0)));
+    }
+    for (u32 g = 0; g < cnt; ++g) {
+        pst[g] = acc;
+        acc += (u64)d.n[g] * (1 + st_levels_of(d.n[g]));
+        roff[g] = racc;
+        racc += d.n[g];
+    }
+    memcpy(host.data() + L.off[0], d.w.data(), 8 * cnt);
+    memcpy(host.data() + L.off[1], d.m.data(), 8 * cnt);
+    memcpy(host.data() + L.off[2], d.n.data(), 4 * cnt);
+    memcpy(host.data() + L.off[3], q.data(), 4 * cnt);
+    memcpy(host.data() + L.off[4], d.dt.data(), cnt);
+    memcpy(host.data() + L.off[5], pst.data(), 8 * cnt);
+    memcpy(host.data() + L.off[6], roff.data(), 8 * cnt);
+    memcpy(host.data() + L.off[7], tiles.data(), 16 * tiles.size());
+    memcpy(host.data() + L.off[8], tasks.data(), 8 * tasks.size());
 }
 
-BatchArgs make_args(const BatchRuntime& rt, void* dev, const size_t off[5], u32 cnt, u32* status)
+BatchArgs make_args(const BatchRuntime& rt, void* dev, const DescLayout& L, u32 cnt, void* arena,
+                    u32* status)
 {
     BatchArgs a;
-    a.wp = (const u32* const*)((char*)dev + off[0]);
-    a.mp = (u32* const*)((char*)dev + off[1]);
-    a.ns = (const u32*)((char*)dev + off[2]);
-    a.queue = (const u32*)((char*)dev + off[3]);
-    a.dts = (const uint8_t*)((char*)dev + off[4]);
+    a.wp = (const u32* const*)((char*)dev + L.off[0]);
+    a.mp = (u32* const*)((char*)dev + L.off[1]);
+    a.ns = (const u32*)((char*)dev + L.off[2]);
+    a.queue = (const u32*)((char*)dev + L.off[3]);
+    a.dts = (const uint8_t*)((char*)dev + L.off[4]);
+    a.pst_off = (const u64*)((char*)dev + L.off[5]);
+    a.row_off = (const u64*)((char*)dev + L.off[6]);
+    a.posst = (u32*)arena;
+    a.best0 = (u64*)((char*)arena + ((L.posst_words * 4 + 7) & ~(size_t)7));
     a.count = cnt;
     a.next = rt.d_next;
     a.slices = rt.d_slices;
@@ -658,14 +805,18 @@ cudaError_t batch_runtime_create(int64_t cap, const BatchTuning& tune, BatchRunt
         e = cudaMemcpy(nr->d_slices, hs.data(), sizeof(SliceWs) * nr->nslices, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMalloc(&nr->d_next, 256);
-    // dynamic shared memory: the fill tile, or per-warp contraction bins for
-    // up to 1024 groups, whichever is larger (the phases reuse it in turn)
-    nr->smem = std::max(fill_smem_bytes((u32)tune.fill_rows),
-                        (size_t)(BATCH_THREADS / 32) * 1024 * sizeof(u64));
+    // dynamic shared memory of k_batched: per-warp contraction bins for up to
+    // 1024 groups (the item path uses the same space as one bin array); the
+    // fill kernel's tile
+    nr->smem = (size_t)(BATCH_THREADS / 32) * 1024 * sizeof(u64);
     nr->bin_cap = (u32)(nr->smem / sizeof(u64));
     nr->warp_bins = (u32)(nr->bin_cap / (BATCH_THREADS / 32));
+    nr->fill_smem = fill_smem_bytes((u32)tune.fill_rows);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nr->smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fill_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)nr->fill_smem);
     if (e != cudaSuccess) {
         batch_runtime_destroy(nr);
         return e;
@@ -682,7 +833,9 @@ void batch_runtime_destroy(BatchRuntime* rt)
     for (auto& kv : rt->plans) {
         cudaGraphExecDestroy(kv.second.exec);
         cudaFree(kv.second.dev);
+        cudaFree(kv.second.arena);
     }
+    cudaFree(rt->arena);
     cudaFree(rt->slice_mem);
     cudaFree(rt->d_slices);
     cudaFree(rt->scratch_mem);
@@ -692,6 +845,21 @@ void batch_runtime_destroy(BatchRuntime* rt)
 }
 
 int64_t batch_runtime_cap(const BatchRuntime* rt) { return rt->cap; }
+
+// Enqueues the batch's kernels on s: round-1 minima of every graph, queue
+// reset, the per-graph MST and leaf order, the fill of every graph.
+static void enqueue_batch(const BatchRuntime& rt, const BatchArgs& a, const void* dev, const DescLayout& L,
+                          cudaStream_t s)
+{
+    if (L.ntasks)
+        k_rowmin_batched<<<L.ntasks, ROWB_THREADS, 0, s>>>(a, (const uint2*)((const char*)dev + L.off[8]));
+    cudaMemsetAsync(rt.d_next, 0, sizeof(u32), s);
+    k_batched<<<rt.nslices, BATCH_THREADS, rt.smem, s>>>(a);
+    if (L.ntiles)
+        k_fill_batched<<<L.ntiles, FILLB_THREADS, rt.fill_smem, s>>>(a, (const uint4*)((const char*)dev + L.off[7]));
+}
+
+static u32 batch_launches(const DescLayout& L) { return 1u + (L.ntasks ? 1u : 0u) + (L.ntiles ? 1u : 0u); }
 
 cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cudaStream_t s,
                          bool cache_graph)
@@ -705,30 +873,37 @@ cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cuda
         inplace |= (d.w[i] == (const void*)d.m[i]);
     if (inplace && (e = ensure_scratch(rt)) != cudaSuccess)
         return e;
-    size_t off[5];
-    const size_t bytes = desc_layout(cnt, off);
-    std::vector<unsigned char> host(bytes);
+    const u32 fr = (u32)rt.tune.fill_rows;
+    const DescLayout L = desc_layout(d, fr);
+    std::vector<unsigned char> host(L.bytes);
     if (!cache_graph) {
-        // one descriptor block per runtime: launches on the runtime are
-        // ordered on its stream, so the next upload follows the last kernel
-        if (rt.desc_bytes < bytes) {
+        // one descriptor block and one arena per runtime: launches on the
+        // runtime are ordered on its stream, so the next upload follows the
+        // last kernel
+        if (rt.desc_bytes < L.bytes) {
             cudaFree(rt.d_desc);
             rt.d_desc = nullptr;
             rt.desc_bytes = 0;
-            if ((e = cudaMalloc(&rt.d_desc, bytes)) != cudaSuccess)
+            if ((e = cudaMalloc(&rt.d_desc, L.bytes)) != cudaSuccess)
                 return e;
-            rt.desc_bytes = bytes;
+            rt.desc_bytes = L.bytes;
         }
-        fill_desc(d, host, off);
+        if (rt.arena_bytes < L.arena_bytes) {
+            cudaFree(rt.arena);
+            rt.arena = nullptr;
+            rt.arena_bytes = 0;
+            if ((e = cudaMalloc(&rt.arena, L.arena_bytes)) != cudaSuccess)
+                return e;
+            rt.arena_bytes = L.arena_bytes;
+        }
+        fill_desc(d, fr, L, host);
         // pageable source: the copy is staged before the call returns
-        if ((e = cudaMemcpyAsync(rt.d_desc, host.data(), bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        if ((e = cudaMemcpyAsync(rt.d_desc, host.data(), L.bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return e;
-        if ((e = cudaMemsetAsync(rt.d_next, 0, sizeof(u32), s)) != cudaSuccess)
-            return e;
-        BatchArgs a = make_args(rt, rt.d_desc, off, cnt, status);
-        prof_launches(1);
+        BatchArgs a = make_args(rt, rt.d_desc, L, cnt, rt.arena, status);
+        prof_launches(batch_launches(L));
         prof_begin(PH_BATCHED, s);
-        k_batched<<<rt.nslices, BATCH_THREADS, rt.smem, s>>>(a);
+        enqueue_batch(rt, a, rt.d_desc, L, s);
         prof_end(PH_BATCHED, s);
         return cudaGetLastError();
     }
@@ -744,20 +919,31 @@ cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cuda
     auto it = rt.plans.find(key);
     if (it == rt.plans.end()) {
         BatchRuntime::Plan p;
-        if ((e = cudaMalloc(&p.dev, bytes)) != cudaSuccess)
+        auto drop = [&]() {
+            cudaFree(p.dev);
+            cudaFree(p.arena);
+        };
+        if ((e = cudaMalloc(&p.dev, L.bytes)) != cudaSuccess)
             return e;
-        fill_desc(d, host, off);
-        if ((e = cudaMemcpy(p.dev, host.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+        if ((e = cudaMalloc(&p.arena, L.arena_bytes)) != cudaSuccess) {
+            drop();
             return e;
-        BatchArgs a = make_args(rt, p.dev, off, cnt, status);
+        }
+        fill_desc(d, fr, L, host);
+        if ((e = cudaMemcpy(p.dev, host.data(), L.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            drop();
+            return e;
+        }
+        BatchArgs a = make_args(rt, p.dev, L, cnt, p.arena, status);
         cudaStream_t cap_s;
-        if ((e = cudaStreamCreateWithFlags(&cap_s, cudaStreamNonBlocking)) != cudaSuccess)
+        if ((e = cudaStreamCreateWithFlags(&cap_s, cudaStreamNonBlocking)) != cudaSuccess) {
+            drop();
             return e;
+        }
         cudaGraph_t graph;
         e = cudaStreamBeginCapture(cap_s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaMemsetAsync(rt.d_next, 0, sizeof(u32), cap_s);
-            k_batched<<<rt.nslices, BATCH_THREADS, rt.smem, cap_s>>>(a);
+            enqueue_batch(rt, a, p.dev, L, cap_s);
             e = cudaStreamEndCapture(cap_s, &graph);
         }
         if (e == cudaSuccess) {
@@ -766,12 +952,12 @@ cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cuda
         }
         cudaStreamDestroy(cap_s);
         if (e != cudaSuccess) {
-            cudaFree(p.dev);
+            drop();
             return e;
         }
         it = rt.plans.emplace(key, p).first;
     }
-    prof_launches(1);
+    prof_launches(batch_launches(L));
     prof_begin(PH_BATCHED, s);
     e = cudaGraphLaunch(it->second.exec, s);
     prof_end(PH_BATCHED, s);

@@ -142,12 +142,24 @@ __device__ __forceinline__ void fill_tile(const u32* __restrict__ pos, const u32
                 __stcs(reinterpret_cast<uint4*>(M + (size_t)i * n + j0 + jj), o);
             }
         } else {
+            // rows not 16-byte aligned (or a narrow tile): 4-byte stores, the
+            // lane's four column ranks kept in registers
+            u32 rk[FC / 32];
+#pragma unroll
+            for (int k = 0; k < FC / 32; ++k)
+                rk[k] = (lane + 32 * k < nc) ? S.rank[lane + 32 * k] : 0u;
             for (u32 r = w; r < nb; r += nthr / 32) {
                 const u32 t = s_t[r], L = s_L[r], R = s_R[r];
                 const u32 i = r0 + rb + r;
-                for (u32 c = lane; c < nc; c += 32) {
-                    u32 v = max(S.T[t][c], S.rank[c] >= t ? R : L);
-                    __stcs(M + (size_t)i * n + j0 + c, (j0 + c == i) ? 0u : bits_of(v, DT));
+                u32* row = M + (size_t)i * n + j0;
+                const u32 dcol = i - j0;   // the diagonal's column in this tile (if < nc)
+#pragma unroll
+                for (int k = 0; k < FC / 32; ++k) {
+                    const u32 c = lane + 32 * k;
+                    if (c < nc) {
+                        const u32 v = max(S.T[t][c], rk[k] >= t ? R : L);
+                        __stcs(row + c, c == dcol ? 0u : bits_of(v, DT));
+                    }
                 }
             }
         }
