@@ -257,7 +257,7 @@ __device__ void contract_level_warps(const ContractArgs& a, u32 cr, u32 cn, u32 
             for (int q = 0; q < 4; ++q)
                 rid[q] = a.members[p + ((u32)q < np ? q : 0)];
             if (LEVEL0) {
-                constexpr int U = 2;
+                constexpr int U = 3;
                 sort_rows4(rid, np);
                 const u32* W = (const u32*)a.cin;
                 const u32 ng = (cr + 3) >> 2;
