@@ -123,6 +123,27 @@ appd_status appd_solve_host(const void *W_host, int64_t n, appd_dtype dt, void *
                             appd_stream_t s);
 
 /*
+ * appd_solve_host_async -- appd_solve_host without the wait, pipelined for a
+ * stream of problems: enqueues the copy of W_host to the device, the solve
+ * (on s) and the copy of M back to M_host, and returns.  Consecutive calls
+ * overlap one call's copy back with the next call's copy in and solve (the
+ * host link carries both directions at once).  The library keeps, per
+ * device, two device buffer pairs (4 x 4 n^2 bytes, until
+ * appd_release_workspaces) and two internal copy streams.  The solve is
+ * ordered on s like appd_solve; the copy back is not: call
+ * appd_solve_host_wait(s) and then synchronize s before reading M_host or
+ * changing W_host.  Pinned host buffers (cudaHostAlloc) reach the link's
+ * bandwidth.  Errors as appd_solve_host.  (Scheduling of this library; no
+ * counterpart in the paper.)
+ */
+appd_status appd_solve_host_async(const void *W_host, int64_t n, appd_dtype dt, void *M_host,
+                                  appd_stream_t s);
+
+/* Makes s wait for the copies back of every appd_solve_host_async call made
+ * so far on this device (enqueues the wait and returns). */
+appd_status appd_solve_host_wait(appd_stream_t s);
+
+/*
  * appd_solve_noalloc -- appd_solve for callers that cannot allocate device
  * memory (a framework that owns a fixed pool or arena, an embedding that does
  * not allow the driver's allocator once it is running).  No counterpart in

@@ -25,8 +25,8 @@ STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD
 
 # every symbol that include/appd.h declares
 EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host",
-           "appd_solve_noalloc", "appd_mst",
-           "appd_leaf_order", "appd_solve_batched", "appd_batched_tuning", "appd_batched_autotune",
+           "appd_solve_host_async", "appd_solve_host_wait", "appd_solve_noalloc", "appd_mst", "appd_leaf_order",
+           "appd_solve_batched", "appd_batched_tuning", "appd_batched_autotune",
            "appd_batched_get_tuning", "appd_check_symmetric",
            "appd_last_device_status", "appd_probe_bounded_wait", "appd_release_workspaces",
            "appd_profile_begin",
@@ -59,6 +59,8 @@ def load(build_if_missing: bool = True):
             "appd_solve": [vp, i64, ci, vp, vp],
             "appd_solve_alg4": [vp, i64, ci, vp, vp],
             "appd_solve_host": [vp, i64, ci, vp, vp],
+            "appd_solve_host_async": [vp, i64, ci, vp, vp],
+            "appd_solve_host_wait": [vp],
             "appd_solve_noalloc": [vp, i64, ci, vp, vp],
             "appd_mst": [vp, i64, ci, vp, vp],
             "appd_leaf_order": [vp, i64, ci, vp, vp, vp],
@@ -158,6 +160,18 @@ def solve_host(W: np.ndarray, stream=None, widest: bool = False) -> np.ndarray:
 def solve_host_ptr(W_ptr: int, n: int, dt: int, M_ptr: int, stream=None):
     """appd_solve_host on raw host pointers (e.g. pinned buffers)."""
     _check(load().appd_solve_host(W_ptr, n, dt, M_ptr, _stream_ptr(stream)), "appd_solve_host")
+
+
+def solve_host_async_ptr(W_ptr: int, n: int, dt: int, M_ptr: int, stream=None):
+    """appd_solve_host_async on raw host pointers: enqueue and return (see
+    solve_host_wait before reading M)."""
+    _check(load().appd_solve_host_async(W_ptr, n, dt, M_ptr, _stream_ptr(stream)),
+           "appd_solve_host_async")
+
+
+def solve_host_wait(stream=None):
+    """Make the stream wait for every pipelined host call's copy back."""
+    _check(load().appd_solve_host_wait(_stream_ptr(stream)), "appd_solve_host_wait")
 
 
 def mst(W, stream=None, widest: bool = False):

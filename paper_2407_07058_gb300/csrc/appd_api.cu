@@ -501,6 +501,127 @@ appd_status appd_solve_host(const void* W_host, int64_t n, appd_dtype dt, void* 
     return e == cudaSuccess ? APPD_OK : cuda_fail(e);
 }
 
+// Pipelined host entry: per device, two copy streams (in, out) and two
+// device buffer pairs; the solve runs on the caller's stream.  One call's
+// copy in and solve overlap the previous call's copy out (the host link
+// carries both directions at once).
+namespace {
+struct HostPipe {
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
+    void* dW[2] = {};
+    void* dM[2] = {};
+    size_t bytes = 0;
+    uint64_t k = 0;
+};
+HostPipe* g_pipe[MAX_DEV] = {};
+std::mutex g_pipe_mu;
+
+void pipe_destroy(HostPipe* p)
+{
+    if (!p)
+        return;
+    for (cudaStream_t st : {p->in, p->out})
+        if (st)
+            cudaStreamSynchronize(st);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(p->dW[i]);
+        cudaFree(p->dM[i]);
+        cudaEventDestroy(p->ev_in[i]);
+        cudaEventDestroy(p->ev_comp[i]);
+        cudaEventDestroy(p->ev_out[i]);
+    }
+    for (cudaStream_t st : {p->in, p->out})
+        if (st)
+            cudaStreamDestroy(st);
+    delete p;
+}
+
+cudaError_t pipe_get(int dev, size_t bytes, HostPipe** out)
+{
+    HostPipe*& p = g_pipe[dev];
+    if (p && p->bytes >= bytes) {
+        *out = p;
+        return cudaSuccess;
+    }
+    pipe_destroy(p);
+    p = new HostPipe();
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t* st : {&p->in, &p->out})
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        for (cudaEvent_t* ev : {&p->ev_in[i], &p->ev_comp[i], &p->ev_out[i]})
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&p->dW[i], bytes);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&p->dM[i], bytes);
+    }
+    if (e != cudaSuccess) {
+        pipe_destroy(p);
+        p = nullptr;
+        return e;
+    }
+    p->bytes = bytes;
+    *out = p;
+    return cudaSuccess;
+}
+}  // namespace
+
+appd_status appd_solve_host_async(const void* W_host, int64_t n, appd_dtype dt, void* M_host,
+                                  appd_stream_t s)
+{
+    appd_status st = check_args(W_host, n, (int)dt, M_host);
+    if (st != APPD_OK || n == 0)
+        return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return APPD_ERR_CUDA;
+    const size_t bytes = (size_t)n * (size_t)n * 4;
+    cudaStream_t cs = (cudaStream_t)s;
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    HostPipe* p = nullptr;
+    cudaError_t e = pipe_get(dev, bytes, &p);
+    if (e != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? APPD_ERR_NOMEM : cuda_fail(e);
+    const int b = (int)(p->k++ & 1);
+    // copy in once this buffer pair's previous copy out is done (which
+    // follows that pair's previous solve)
+    if ((e = cudaStreamWaitEvent(p->in, p->ev_out[b], 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p->dW[b], W_host, bytes, cudaMemcpyHostToDevice, p->in)) != cudaSuccess ||
+        (e = cudaEventRecord(p->ev_in[b], p->in)) != cudaSuccess)
+        return cuda_fail(e);
+    // the solve, on s: after the copy in and after the pair's M was copied out
+    if ((e = cudaStreamWaitEvent(cs, p->ev_in[b], 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(cs, p->ev_out[b], 0)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((st = solve_impl(p->dW[b], n, (int)dt, p->dM[b], cs, false)) != APPD_OK)
+        return st;
+    if ((e = cudaEventRecord(p->ev_comp[b], cs)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->out, p->ev_comp[b], 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(M_host, p->dM[b], bytes, cudaMemcpyDeviceToHost, p->out)) != cudaSuccess ||
+        (e = cudaEventRecord(p->ev_out[b], p->out)) != cudaSuccess)
+        return cuda_fail(e);
+    return APPD_OK;
+}
+
+appd_status appd_solve_host_wait(appd_stream_t s)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return APPD_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    HostPipe* p = g_pipe[dev];
+    if (!p)
+        return APPD_OK;
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        e = cudaStreamWaitEvent((cudaStream_t)s, p->ev_out[b], 0);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
 appd_status appd_mst(const void* W, int64_t n, appd_dtype dt, uint64_t* edges_out, appd_stream_t s)
 {
     appd_status st = check_args(W, n, (int)dt, edges_out);
@@ -726,6 +847,11 @@ appd_status appd_release_workspaces(void)
     }
     batch_runtime_destroy(g_brt[dev]);
     g_brt[dev] = nullptr;
+    {
+        std::lock_guard<std::mutex> lp(g_pipe_mu);
+        pipe_destroy(g_pipe[dev]);
+        g_pipe[dev] = nullptr;
+    }
     return APPD_OK;
 }
 
