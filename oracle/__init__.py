@@ -13,6 +13,7 @@ return the matrix of original weight bits in the same dtype (diagonal 0):
 - ``brute(W)``: all simple paths, Eq. 1-2, n <= 9.
 - ``prim(W)``: Prim order and the MST edge codes.
 - ``tree_rows(W, mst, sources)``: rows of M by traversing the MST.
+- ``insert(M, w)``: warm start, the matrix of G + p from G's (Section 6.1).
 
 Every function takes ``widest=True`` for the widest-path matrix (Section 4.2:
 the largest possible smallest edge weight over all paths), computed by the
@@ -62,6 +63,7 @@ def _lib():
             lib.appd_oracle_brute.argtypes = [vp, i64, ci, vp]
             lib.appd_oracle_prim.argtypes = [vp, i64, ci, vp, vp]
             lib.appd_oracle_tree_rows.argtypes = [vp, i64, ci, vp, vp, i64, vp]
+            lib.appd_oracle_insert.argtypes = [vp, i64, ci, vp, vp]
             lib.appd_oracle_set_mutation.argtypes = [ci]
             lib.appd_oracle_order_key.argtypes = [ctypes.c_uint32, ci]
             lib.appd_oracle_order_key.restype = ctypes.c_uint32
@@ -140,6 +142,19 @@ def tree_rows(W: np.ndarray, mst: np.ndarray, sources, widest: bool = False) -> 
     _check(_lib().appd_oracle_tree_rows(Wc.ctypes.data, n, dt, mst.ctypes.data, src.ctypes.data,
                                         len(src), rows.ctypes.data), "appd_oracle_tree_rows")
     return rows
+
+
+def insert(M: np.ndarray, w: np.ndarray, widest: bool = False) -> np.ndarray:
+    """Warm start (Section 6.1): the matrix of G + p from G's matrix M and the
+    weights w of p's edges; p becomes the last index."""
+    Mc, n, dt = _prep(M, widest)
+    wc = np.ascontiguousarray(np.asarray(w, dtype=Mc.dtype))
+    if wc.shape != (n,):
+        raise ValueError("w must hold one weight per vertex")
+    out = np.empty((n + 1, n + 1), dtype=Mc.dtype)
+    _check(_lib().appd_oracle_insert(Mc.ctypes.data, n, dt, wc.ctypes.data, out.ctypes.data),
+           "appd_oracle_insert")
+    return out
 
 
 def order_key(bits: int, dtype: int) -> int:

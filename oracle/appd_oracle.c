@@ -36,6 +36,16 @@
  * removal runs from the smallest weight up, and every routine below computes
  * the widest-path matrix.  The output cells still hold original bits.
  *
+ * Warm start (Section 6.1): given M for a graph G and the weights w(k) of a
+ * new vertex p's edges, the matrix of G + p follows without recomputing the
+ * tree.  A path from i to p ends with one edge k-p, so the distance to p is
+ * d(i) = min over k of max(M(i,k), w(k)) (M(i,i) counts as the empty path);
+ * a path between old vertices either avoids p (M(i,j) is the best such) or
+ * passes through it once (max(d(i), d(j)) is the best such), so the new
+ * M'(i,j) = min(M(i,j), max(d(i), d(j))).  appd_oracle_insert applies this
+ * recurrence with plain loops; it is pinned against solving G + p from
+ * scratch.
+ *
  * Test-only routines in this file: the ascending (small-to-large) form of
  * Section 3, the (min,max) Floyd-Warshall variant named in Section 1 and
  * Table 1, brute-force enumeration of simple paths (Eq. 1-2 written out),
@@ -533,6 +543,55 @@ int appd_oracle_tree_rows(const uint32_t *W, int64_t n, int dtype, const uint64_
     free(best);
     free(seen);
     free_adj(&t);
+    return 0;
+}
+
+/* ------------------------------------------- warm start (Section 6.1) */
+/*
+ * M (n x n, a solved matrix), w (n weights of the new vertex's edges) ->
+ * Mout ((n+1) x (n+1)), the new vertex is index n.  Keys decide, the cells
+ * keep the selected weight's bits; the diagonal is all-zero bits.
+ */
+int appd_oracle_insert(const uint32_t *M, int64_t n, int dtype, const uint32_t *w, uint32_t *Mout)
+{
+    if (n < 0 || n > 65535)
+        return -1;
+    uint32_t *d = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+    if (!d)
+        return -2;
+    for (int64_t i = 0; i < n; ++i) {
+        /* k == i: the path i - p itself */
+        uint32_t best_k = order_key(w[i], dtype), best_b = w[i];
+        for (int64_t k = 0; k < n; ++k) {
+            if (k == i)
+                continue;
+            uint32_t km = order_key(M[i * n + k], dtype), kw = order_key(w[k], dtype);
+            uint32_t mk = km > kw ? km : kw;
+            uint32_t mb = km > kw ? M[i * n + k] : w[k];
+            if (mk < best_k) {
+                best_k = mk;
+                best_b = mb;
+            }
+        }
+        d[i] = best_b;
+    }
+    const int64_t m = n + 1;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            if (i == j) {
+                Mout[i * m + j] = 0;
+                continue;
+            }
+            uint32_t ki = order_key(d[i], dtype), kj = order_key(d[j], dtype);
+            uint32_t via_k = ki > kj ? ki : kj, via_b = ki > kj ? d[i] : d[j];
+            uint32_t km = order_key(M[i * n + j], dtype);
+            Mout[i * m + j] = km <= via_k ? M[i * n + j] : via_b;
+        }
+        Mout[i * m + n] = d[i];
+        Mout[n * m + i] = d[i];
+    }
+    Mout[n * m + n] = 0;
+    free(d);
     return 0;
 }
 
