@@ -162,6 +162,23 @@ appd_status appd_solve_host_wait(appd_stream_t s);
 appd_status appd_solve_noalloc(const void *W, int64_t n, appd_dtype dt, void *M, appd_stream_t s);
 
 /*
+ * appd_insert_vertex -- warm start (Section 6.1): the matrix of G + p from
+ * the matrix of G and the new vertex's edge weights, without a new tree.
+ *   M      device, n x n: the result of appd_solve (same dtype) for G.
+ *   w      device, n weights: w[k] = weight of the edge between vertex k and p.
+ *   M_out  device, (n+1) x (n+1), row-major: the matrix of G + p, where p is
+ *          vertex n.  Must not overlap M or w (APPD_ERR_ALIAS).
+ * With d(i) = min over k of max(M(i,k), w[k]) (the k = i term is w[i]),
+ * M_out(i,j) = min(M(i,j), max(d(i), d(j))), M_out(i,n) = M_out(n,i) = d(i),
+ * all-zero diagonal; comparisons and the widest dtypes as appd_solve.  The
+ * result equals appd_solve on the (n+1)-vertex graph, bit for bit.  Two
+ * streaming passes over M.  0 <= n <= 65536 (n == 0: M and w may be NULL,
+ * M_out becomes the 1 x 1 zero matrix); n > 65536 returns APPD_ERR_TOO_LARGE.
+ */
+appd_status appd_insert_vertex(const void *M, int64_t n, appd_dtype dt, const void *w, void *M_out,
+                               appd_stream_t s);
+
+/*
  * appd_mst -- the minimum spanning tree computed by the solve's MST stage.
  *   edges_out  device pointer to n-1 uint64 values; each is
  *              key << 32 | lo << 16 | hi, where lo < hi are the endpoints and

@@ -554,7 +554,7 @@ int appd_oracle_tree_rows(const uint32_t *W, int64_t n, int dtype, const uint64_
  */
 int appd_oracle_insert(const uint32_t *M, int64_t n, int dtype, const uint32_t *w, uint32_t *Mout)
 {
-    if (n < 0 || n > 65535)
+    if (n < 0 || n > 65536)
         return -1;
     uint32_t *d = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n + 1));
     if (!d)

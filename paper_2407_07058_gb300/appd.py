@@ -25,7 +25,7 @@ STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD
 
 # every symbol that include/appd.h declares
 EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host",
-           "appd_solve_host_async", "appd_solve_host_wait", "appd_solve_noalloc", "appd_mst", "appd_leaf_order",
+           "appd_solve_host_async", "appd_solve_host_wait", "appd_solve_noalloc", "appd_insert_vertex", "appd_mst", "appd_leaf_order",
            "appd_solve_batched", "appd_batched_tuning", "appd_batched_autotune",
            "appd_batched_get_tuning", "appd_check_symmetric",
            "appd_last_device_status", "appd_probe_bounded_wait", "appd_release_workspaces",
@@ -61,6 +61,7 @@ def load(build_if_missing: bool = True):
             "appd_solve_host": [vp, i64, ci, vp, vp],
             "appd_solve_host_async": [vp, i64, ci, vp, vp],
             "appd_solve_host_wait": [vp],
+            "appd_insert_vertex": [vp, i64, ci, vp, vp, vp],
             "appd_solve_noalloc": [vp, i64, ci, vp, vp],
             "appd_mst": [vp, i64, ci, vp, vp],
             "appd_leaf_order": [vp, i64, ci, vp, vp, vp],
@@ -160,6 +161,21 @@ def solve_host(W: np.ndarray, stream=None, widest: bool = False) -> np.ndarray:
 def solve_host_ptr(W_ptr: int, n: int, dt: int, M_ptr: int, stream=None):
     """appd_solve_host on raw host pointers (e.g. pinned buffers)."""
     _check(load().appd_solve_host(W_ptr, n, dt, M_ptr, _stream_ptr(stream)), "appd_solve_host")
+
+
+def insert_vertex(M, w, out=None, stream=None, widest: bool = False):
+    """Warm start (Section 6.1): the (n+1) x (n+1) matrix of G + p from G's
+    matrix M (n x n, from solve) and the n weights w of p's edges."""
+    import torch
+    n = _square_cuda(M)
+    if not w.is_cuda or w.numel() != n or w.dtype != M.dtype:
+        raise ValueError("w must be a CUDA vector of n weights of M's dtype")
+    Mo = torch.empty((n + 1, n + 1), dtype=M.dtype, device=M.device) if out is None else out
+    dt = _dtype_code(M) | (WIDEST if widest else 0)
+    with torch.cuda.device(M.device):
+        _check(load().appd_insert_vertex(M.data_ptr(), n, dt, w.contiguous().data_ptr(), Mo.data_ptr(),
+                                         _stream_ptr(stream)), "appd_insert_vertex")
+    return Mo
 
 
 def solve_host_async_ptr(W_ptr: int, n: int, dt: int, M_ptr: int, stream=None):

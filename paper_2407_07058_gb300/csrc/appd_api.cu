@@ -622,6 +622,30 @@ appd_status appd_solve_host_wait(appd_stream_t s)
     return e == cudaSuccess ? APPD_OK : cuda_fail(e);
 }
 
+appd_status appd_insert_vertex(const void* M, int64_t n, appd_dtype dt, const void* w, void* M_out,
+                               appd_stream_t s)
+{
+    if (n < 0 || (n > 0 && (!M || !w)) || !M_out || !dtype_ok((int)dt))
+        return APPD_ERR_INVALID;
+    if (n > 65536)
+        return APPD_ERR_TOO_LARGE;
+    const char* o = (const char*)M_out;
+    const size_t ob = (size_t)(n + 1) * (size_t)(n + 1) * 4;
+    auto overlaps = [&](const void* p, size_t bytes) {
+        const char* a = (const char*)p;
+        return a < o + ob && o < a + bytes;
+    };
+    if (overlaps(M, (size_t)n * (size_t)n * 4) || overlaps(w, (size_t)n * 4))
+        return APPD_ERR_ALIAS;
+    std::lock_guard<std::mutex> lk(g_mu);
+    SolveCtx c;
+    appd_status st = prepare(n > 0 ? n : 1, c);
+    if (st != APPD_OK)
+        return st;
+    cudaError_t e = run_insert(M, n, (int)dt, w, M_out, c.ws->hook, c.ws->sms, (cudaStream_t)s);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
 appd_status appd_mst(const void* W, int64_t n, appd_dtype dt, uint64_t* edges_out, appd_stream_t s)
 {
     appd_status st = check_args(W, n, (int)dt, edges_out);

@@ -84,6 +84,9 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
 cudaError_t run_leaf_order(Workspace& ws, u32* status, cudaStream_t s);
 cudaError_t run_fill(Workspace& ws, int dt, void* M, cudaStream_t s);
 cudaError_t run_fill_alg4(Workspace& ws, int dt, void* M, u32* status, cudaStream_t s);
+// warm start (insert.cu): M' ((n+1) x (n+1)) from M (n x n) and w (n); d: n u32 scratch
+cudaError_t run_insert(const void* M, int64_t n, int dt, const void* w, void* Mo, u32* d, int sms,
+                       cudaStream_t s);
 cudaError_t run_fill_trivial(int64_t n, void* M, cudaStream_t s);   // n == 1
 
 // profiling (appd_profile_begin/end): phases of a solve
