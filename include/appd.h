@@ -305,13 +305,16 @@ appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_s
 
 /* Admit a request for an n-vertex graph of dtype dt.  On APPD_OK, *req_id is
  * its id and *W_slot a device pointer to n*n elements that the caller fills
- * (on any stream, synchronized before commit) and must not touch after
- * commit.  Returns APPD_ERR_BUSY if the budget or slot count is exhausted. */
-appd_status appd_server_submit(appd_server *sv, int64_t n, appd_dtype dt, uint64_t *req_id,
-                               void **W_slot);
+ * on stream s (s is made to wait for the slot's allocation; no host wait)
+ * and must not touch after commit.  Returns APPD_ERR_BUSY if the budget or
+ * slot count is exhausted. */
+appd_status appd_server_submit(appd_server *sv, int64_t n, appd_dtype dt, appd_stream_t s,
+                               uint64_t *req_id, void **W_slot);
 
-/* Queue an admitted request for solving. */
-appd_status appd_server_commit(appd_server *sv, uint64_t req_id);
+/* Queue an admitted request for solving: its W is complete once the work
+ * enqueued on s before this call has run (the solve waits for that on the
+ * device; the caller need not synchronize). */
+appd_status appd_server_commit(appd_server *sv, uint64_t req_id, appd_stream_t s);
 
 /* Collect finished requests: up to cap ids in done_ids and their device M
  * pointers in M_ptrs (valid until release); *n_done receives the count.

@@ -75,8 +75,8 @@ def load(build_if_missing: bool = True):
             "appd_probe_bounded_wait": [i32, vp],
             "appd_release_workspaces": [],
             "appd_server_create": [ctypes.c_size_t, i32, ctypes.POINTER(vp)],
-            "appd_server_submit": [vp, i64, ci, ctypes.POINTER(u64), ctypes.POINTER(vp)],
-            "appd_server_commit": [vp, u64],
+            "appd_server_submit": [vp, i64, ci, vp, ctypes.POINTER(u64), ctypes.POINTER(vp)],
+            "appd_server_commit": [vp, u64, vp],
             "appd_server_poll": [vp, vp, vp, i32, ctypes.POINTER(i32)],
             "appd_server_release": [vp, u64],
             "appd_server_destroy": [vp],
@@ -313,18 +313,22 @@ class Server:
         _check(load().appd_server_create(budget_bytes, max_inflight, ctypes.byref(self._h)),
                "appd_server_create")
 
-    def submit(self, n: int, dt: int):
-        """Returns (req_id, W_slot_ptr) or None when admission is refused (busy)."""
+    def submit(self, n: int, dt: int, stream=None):
+        """Returns (req_id, W_slot_ptr) or None when admission is refused (busy).
+        Fill the slot on `stream` (default: the current stream)."""
         rid = ctypes.c_uint64()
         slot = ctypes.c_void_p()
-        code = load().appd_server_submit(self._h, n, dt, ctypes.byref(rid), ctypes.byref(slot))
+        code = load().appd_server_submit(self._h, n, dt, _stream_ptr(stream), ctypes.byref(rid),
+                                         ctypes.byref(slot))
         if code == 7:
             return None
         _check(code, "appd_server_submit")
         return rid.value, slot.value
 
-    def commit(self, rid: int):
-        _check(load().appd_server_commit(self._h, rid), "appd_server_commit")
+    def commit(self, rid: int, stream=None):
+        """Queue the request; its W is complete after the work already on
+        `stream` (default: the current stream)."""
+        _check(load().appd_server_commit(self._h, rid, _stream_ptr(stream)), "appd_server_commit")
 
     def poll(self, cap: int = 1024):
         ids = (ctypes.c_uint64 * cap)()

@@ -245,10 +245,12 @@ __device__ void contract_level_warps(const ContractArgs& a, u32 cr, u32 cn, u32 
 {
     const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     u64* bins = wbins + (size_t)wid * wcap;
+    // bins start empty once per level; each group's write-out empties them
+    // again for the warp's next group
+    for (u32 b = lane; b < cn; b += 32)
+        bins[b] = EDGE_INF;
+    __syncwarp();
     for (u32 A = wid; A < cn; A += nw) {
-        for (u32 b = lane; b < cn; b += 32)
-            bins[b] = EDGE_INF;
-        __syncwarp();
         const u32 m0 = a.gstart[A], m1 = a.gstart[A + 1];
         for (u32 p = m0; p < m1; p += 4) {
             const u32 np = min(4u, m1 - p);
@@ -351,6 +353,7 @@ __device__ void contract_level_warps(const ContractArgs& a, u32 cr, u32 cn, u32 
         for (u32 b = lane; b < cn; b += 32) {
             const u64 v = bins[b];
             dst[b] = v;
+            bins[b] = EDGE_INF;
             m = v < m ? v : m;
         }
         m = warp_min_u64(m);

@@ -42,6 +42,7 @@ struct Req {
     void* W = nullptr;
     void* M = nullptr;
     size_t bytes = 0;
+    cudaEvent_t ready = nullptr;   // recorded on the caller's stream at commit
     bool committed = false;
     bool done = false;
 };
@@ -68,6 +69,8 @@ struct appd_server {
     uint64_t next_id = 1;
     int device = 0;
     cudaStream_t alloc_stream = nullptr;
+    cudaEvent_t alloc_done = nullptr;             // the latest slot allocation
+    std::vector<cudaEvent_t> event_pool;          // commit events, reused
     Slot slots[NSLOT];
     std::unordered_map<uint64_t, Req> reqs;
     std::deque<uint64_t> pending;    // committed, not yet launched
@@ -138,10 +141,24 @@ void dispatch_loop(appd_server* sv)
             std::vector<Req> bigreq;
             for (uint64_t id : big)
                 bigreq.push_back(sv->reqs[id]);
+            std::vector<cudaEvent_t> ready;
+            for (uint64_t id : ids) {
+                Req& r = sv->reqs[id];
+                if (r.ready) {
+                    ready.push_back(r.ready);
+                    r.ready = nullptr;
+                }
+            }
             free_slot->launching = true;
             free_slot->ids = ids;
             lk.unlock();
-            cudaError_t e = batch_launch(*free_slot->rt, d, sv->status, free_slot->stream, false);
+            // the batch starts after every request's W is complete
+            cudaError_t e = cudaSuccess;
+            for (cudaEvent_t ev : ready)
+                if (e == cudaSuccess)
+                    e = cudaStreamWaitEvent(free_slot->stream, ev, 0);
+            if (e == cudaSuccess)
+                e = batch_launch(*free_slot->rt, d, sv->status, free_slot->stream, false);
             int st = APPD_OK;
             for (const Req& r : bigreq) {
                 if (st != APPD_OK)
@@ -151,6 +168,8 @@ void dispatch_loop(appd_server* sv)
             }
             cudaError_t e2 = cudaEventRecord(free_slot->done, free_slot->stream);
             lk.lock();
+            // the waits are enqueued: the events may be recorded again
+            sv->event_pool.insert(sv->event_pool.end(), ready.begin(), ready.end());
             // only now may retire() look at the event: it belongs to this batch
             free_slot->launching = false;
             free_slot->busy = true;
@@ -183,6 +202,8 @@ appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_s
         std::lock_guard<std::mutex> lk(sv->mu);
     }
     cudaError_t e = cudaStreamCreateWithFlags(&sv->alloc_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&sv->alloc_done, cudaEventDisableTiming);
     for (Slot& sl : sv->slots) {
         if (e == cudaSuccess)
             e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
@@ -206,8 +227,8 @@ appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_s
     return APPD_OK;
 }
 
-appd_status appd_server_submit(appd_server* sv, int64_t n, appd_dtype dt, uint64_t* req_id,
-                               void** W_slot)
+appd_status appd_server_submit(appd_server* sv, int64_t n, appd_dtype dt, appd_stream_t s,
+                               uint64_t* req_id, void** W_slot)
 {
     if (!sv || !req_id || !W_slot || n <= 0 || !dtype_ok((int)dt))
         return APPD_ERR_INVALID;
@@ -226,13 +247,15 @@ appd_status appd_server_submit(appd_server* sv, int64_t n, appd_dtype dt, uint64
     r.n = n;
     r.dt = dt;
     r.bytes = bytes;
+    std::lock_guard<std::mutex> lk(sv->mu);
     cudaError_t e = cudaMallocAsync(&r.W, bytes, sv->alloc_stream);
     if (e == cudaSuccess)
         e = cudaMallocAsync(&r.M, bytes, sv->alloc_stream);
-    // the caller may fill W from any stream: make the slot valid first
+    // the caller fills W on s: s waits for the allocation (no host wait)
     if (e == cudaSuccess)
-        e = cudaStreamSynchronize(sv->alloc_stream);
-    std::lock_guard<std::mutex> lk(sv->mu);
+        e = cudaEventRecord(sv->alloc_done, sv->alloc_stream);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent((cudaStream_t)s, sv->alloc_done, 0);
     if (e != cudaSuccess) {
         if (r.W)
             cudaFreeAsync(r.W, sv->alloc_stream);
@@ -247,7 +270,7 @@ appd_status appd_server_submit(appd_server* sv, int64_t n, appd_dtype dt, uint64
     return APPD_OK;
 }
 
-appd_status appd_server_commit(appd_server* sv, uint64_t req_id)
+appd_status appd_server_commit(appd_server* sv, uint64_t req_id, appd_stream_t s)
 {
     if (!sv)
         return APPD_ERR_INVALID;
@@ -258,6 +281,18 @@ appd_status appd_server_commit(appd_server* sv, uint64_t req_id)
             return APPD_ERR_NOT_FOUND;
         if (it->second.committed)
             return APPD_ERR_INVALID;
+        cudaEvent_t ev = nullptr;
+        if (!sv->event_pool.empty()) {
+            ev = sv->event_pool.back();
+            sv->event_pool.pop_back();
+        } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            return APPD_ERR_CUDA;
+        }
+        if (cudaEventRecord(ev, (cudaStream_t)s) != cudaSuccess) {
+            sv->event_pool.push_back(ev);
+            return APPD_ERR_CUDA;
+        }
+        it->second.ready = ev;
         it->second.committed = true;
         sv->pending.push_back(req_id);
     }
@@ -325,7 +360,13 @@ appd_status appd_server_destroy(appd_server* sv)
     for (auto& kv : sv->reqs) {
         cudaFreeAsync(kv.second.W, sv->alloc_stream);
         cudaFreeAsync(kv.second.M, sv->alloc_stream);
+        if (kv.second.ready)
+            cudaEventDestroy(kv.second.ready);
     }
+    for (cudaEvent_t ev : sv->event_pool)
+        cudaEventDestroy(ev);
+    if (sv->alloc_done)
+        cudaEventDestroy(sv->alloc_done);
     if (sv->alloc_stream) {
         cudaStreamSynchronize(sv->alloc_stream);
         cudaStreamDestroy(sv->alloc_stream);

@@ -113,13 +113,36 @@ def test_server_admission_and_release_rules():
         sv.close()
 
 
+@pytest.mark.gpu
+def test_server_stream_ordered_ingress_without_host_sync():
+    # slots filled by kernels on a side stream, committed on that stream with
+    # no host synchronization: every solve must wait for its generation
+    side = torch.cuda.Stream()
+    specs = [(3000, appd.U32), (500, appd.U32), (4097, appd.U32), (64, appd.U32), (1500, appd.U32)]
+    sv = appd.Server(4 << 30, 64)
+    try:
+        ids = []
+        for k, (n, dt) in enumerate(specs):
+            rid, slot = sv.submit(n, dt, side)
+            synth.device_hash_u32(70 + k, n, slot, side.cuda_stream)
+            sv.commit(rid, side)
+            ids.append(rid)
+        done = _wait(sv, len(ids))
+        for k, (rid, (n, dt)) in enumerate(zip(ids, specs)):
+            got = _read(done[rid], n, np.uint32)
+            assert np.array_equal(got, oracle.appd(synth.hash_u32(n, seed=70 + k))), f"n={n}"
+            sv.release(rid)
+    finally:
+        sv.close()
+
+
 def test_server_argument_errors_need_no_gpu():
     lib = appd.load()
     import ctypes
     h = ctypes.c_void_p()
     assert lib.appd_server_create(0, 4, ctypes.byref(h)) == 1
     assert lib.appd_server_create(1 << 30, 0, ctypes.byref(h)) == 1
-    assert lib.appd_server_submit(None, 10, 0, None, None) == 1
-    assert lib.appd_server_commit(None, 1) == 1
+    assert lib.appd_server_submit(None, 10, 0, None, None, None) == 1
+    assert lib.appd_server_commit(None, 1, None) == 1
     assert lib.appd_server_release(None, 1) == 1
     assert lib.appd_server_destroy(None) == 1
