@@ -443,12 +443,12 @@ def run_ours(args, rank, world, local):
     c1 = prof["c1"]
     # algorithmic bytes per launch: the round-1 minima and the level-0
     # contraction read the upper triangle of W (2 n (n-1) bytes), the latter
-    # writes P (8 c1^2) and symmetrizes it in place (read + write 16 c1^2);
-    # the fill writes M (4 n^2)
+    # writes P (8 c1^2) whose column minima are read back (8 c1^2); the fill
+    # writes M (4 n^2)
     tri = 2.0 * n * (n - 1)
     cand = {
         "k_fill": (prof["fill"], 4.0 * n * n),
-        "k_contract(W)+k_sym_c1": (prof["contract_w"], tri + 24.0 * c1 * c1),
+        "k_contract(W)+k_colmin_p": (prof["contract_w"], tri + 16.0 * c1 * c1),
         "k_rowmin_sym": (prof["rowmin"], tri),
     }
     dom = max(cand, key=lambda k: cand[k][0])

@@ -349,8 +349,10 @@ __device__ __forceinline__ void fold_upper(const uint4* v, const u32* rid, u32 j
 // rows[q].  rows[] is ascending, so columns j <= rows[0] are skipped, row 0
 // is valid wherever any row is (it seeds each column's minimum), and a
 // row's column groups that lie wholly at or left of its diagonal are not
-// loaded.  The result P(A, B) covers pairs a < b only; the symmetric
-// C_1(A, B) = min(P(A, B), P(B, A)) is formed afterwards (k_sym_c1).
+// loaded.  The result P(A, B) covers pairs a < b only, so
+// C_1(A, B) = min(P(A, B), P(B, A)): C_1's row minima are P's row minima
+// (this epilogue) folded with P's column minima (k_colmin_p), and level 1
+// contracts P itself and symmetrizes its much smaller result (k_sym).
 template <int DT>
 __device__ __forceinline__ void contract_cols_w_upper(const u32* __restrict__ Wp, u32 cr,
                                                       const u32* __restrict__ label,
@@ -496,11 +498,9 @@ __device__ __forceinline__ void contract_item(const ContractArgs& a, u32 item, u
             atomicMin(dst + b, v);
         m = v < m ? v : m;
     }
-    if (!UPPER) {
-        m = block_min_u64(m, s_red);
-        if (tid == 0 && m != EDGE_INF)
-            atomicMin(&a.best_out[A], m);
-    }
+    m = block_min_u64(m, s_red);
+    if (tid == 0 && m != EDGE_INF)
+        atomicMin(&a.best_out[A], m);
     __syncthreads();
 }
 

@@ -31,46 +31,20 @@ int ceil_log2(int64_t x)
 }
 
 // ------------------------------------------------------------ round 1 (K1)
-// One CTA per row (grid-stride).  The tie-break inside one row is "smaller
-// column wins", which equals the packed order for a fixed row.
-template <int DT, bool VEC>
-__global__ void __launch_bounds__(256) k_rowmin(const u32* __restrict__ W, u32 n,
-                                                u64* __restrict__ best)
+// General form (rows not 16-byte aligned): one CTA per row (grid-stride).
+// The tie-break inside one row is "smaller column wins", which equals the
+// packed order for a fixed row.
+template <int DT>
+__global__ void __launch_bounds__(256) k_rowmin(const u32* __restrict__ W, u32 n, u64* __restrict__ best)
 {
     __shared__ u64 sh[32];
     for (u32 row = blockIdx.x; row < n; row += gridDim.x) {
         const u32* r = W + (size_t)row * n;
         u64 m = EDGE_INF;
-        auto take = [&](u32 bits, u32 j) {
-            u64 c = ((u64)key_of(bits, DT) << 32) | j;
+        for (u32 j = threadIdx.x; j < n; j += 256) {
+            const u64 c = ((u64)key_of(ld_stream_u32(r + j), DT) << 32) | j;
             if (j != row && c < m)
                 m = c;
-        };
-        if (VEC) {
-            const u32 n4 = n >> 2;
-            u32 g = threadIdx.x;
-            for (; g + 3 * 256 < n4; g += 4 * 256) {
-                uint4 v0 = ld_stream_v4(r + 4 * g);
-                uint4 v1 = ld_stream_v4(r + 4 * (g + 256));
-                uint4 v2 = ld_stream_v4(r + 4 * (g + 512));
-                uint4 v3 = ld_stream_v4(r + 4 * (g + 768));
-                take(v0.x, 4 * g), take(v0.y, 4 * g + 1), take(v0.z, 4 * g + 2), take(v0.w, 4 * g + 3);
-                u32 b1 = 4 * (g + 256);
-                take(v1.x, b1), take(v1.y, b1 + 1), take(v1.z, b1 + 2), take(v1.w, b1 + 3);
-                u32 b2 = 4 * (g + 512);
-                take(v2.x, b2), take(v2.y, b2 + 1), take(v2.z, b2 + 2), take(v2.w, b2 + 3);
-                u32 b3 = 4 * (g + 768);
-                take(v3.x, b3), take(v3.y, b3 + 1), take(v3.z, b3 + 2), take(v3.w, b3 + 3);
-            }
-            for (; g < n4; g += 256) {
-                uint4 v = ld_stream_v4(r + 4 * g);
-                take(v.x, 4 * g), take(v.y, 4 * g + 1), take(v.z, 4 * g + 2), take(v.w, 4 * g + 3);
-            }
-            for (u32 j = 4 * n4 + threadIdx.x; j < n; j += 256)
-                take(r[j], j);
-        } else {
-            for (u32 j = threadIdx.x; j < n; j += 256)
-                take(ld_stream_u32(r + j), j);
         }
         m = block_min_u64(m, sh);
         if (threadIdx.x == 0)
@@ -249,22 +223,61 @@ __global__ void __launch_bounds__(TWO ? CONTRACT_THREADS2 : CONTRACT_THREADS, TW
     }
 }
 
-// After the upper-triangle level-0 contraction, P(A, B) holds the minimum
-// over pairs a in A, b in B with a < b, so C_1(A, B) = min(P(A, B), P(B, A)).
-// Each CTA takes tile pairs (ti <= tj) of SYM_T x SYM_T, writes the minimum
-// to both tiles in place (no other CTA touches them), and folds C_1's row
-// minima -- the next round's best edges -- into best_out with atomic minima.
+// The level-0 contraction over the upper triangle leaves P with P(A, B) =
+// min over pairs a in A, b in B with a < b, so C_1(A, B) = min(P(A, B),
+// P(B, A)).  C_1 is never formed: its row minima (the round-1 best edges)
+// are P's row minima (the contraction's epilogue) folded with P's column
+// minima (k_colmin_p); level 1 contracts P itself into Q, with
+// Q(X, Y) = min over A in X, B in Y of P(A, B), so C_2(X, Y) =
+// min(Q(X, Y), Q(Y, X)), which k_sym forms in place (C_2 is small) together
+// with C_2's row minima.
+constexpr u32 CMIN_ROWS = 256, CMIN_THREADS = 256;
+
+__global__ void __launch_bounds__(CMIN_THREADS) k_colmin_p(const u64* __restrict__ P, Counters* ctr,
+                                                           u64* __restrict__ best_out)
+{
+    if (*(volatile u32*)&ctr->done)
+        return;
+    const u32 cn = ((volatile u32*)ctr->c)[1];
+    const u32 j = blockIdx.x * CMIN_THREADS + threadIdx.x;
+    const u32 r0 = blockIdx.y * CMIN_ROWS;
+    if (j >= cn || r0 >= cn)
+        return;
+    const u32 r1 = min(cn, r0 + CMIN_ROWS);
+    u64 m = EDGE_INF;
+    u32 r = r0;
+    for (; r + 8 <= r1; r += 8) {
+        u64 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            v[q] = P[(size_t)(r + q) * cn + j];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            m = v[q] < m ? v[q] : m;
+    }
+    for (; r < r1; ++r) {
+        const u64 v = P[(size_t)r * cn + j];
+        m = v < m ? v : m;
+    }
+    if (m != EDGE_INF)
+        atomicMin(&best_out[j], m);
+}
+
+// In-place symmetrization of C_{level+1} (row stride |C_{level+1}|): each CTA
+// takes tile pairs (ti <= tj) of SYM_T x SYM_T, writes the minimum to both
+// tiles (no other CTA touches them), and folds the row minima into best_out
+// with atomic minima.
 constexpr u32 SYM_T = 64, SYM_THREADS = 512;
 
-__global__ void __launch_bounds__(SYM_THREADS) k_sym_c1(u64* __restrict__ C, Counters* ctr,
-                                                        u64* __restrict__ best_out)
+__global__ void __launch_bounds__(SYM_THREADS) k_sym(u64* __restrict__ C, Counters* ctr, int level,
+                                                     u64* __restrict__ best_out)
 {
     extern __shared__ __align__(16) u64 s_sym[];
     u64(*s_a)[SYM_T + 1] = reinterpret_cast<u64(*)[SYM_T + 1]>(s_sym);
     u64(*s_b)[SYM_T + 1] = reinterpret_cast<u64(*)[SYM_T + 1]>(s_sym + SYM_T * (SYM_T + 1));
     if (*(volatile u32*)&ctr->done)
         return;
-    const u32 cn = ((volatile u32*)ctr->c)[1];
+    const u32 cn = ((volatile u32*)ctr->c)[level + 1];
     const u32 T = (cn + SYM_T - 1) / SYM_T;
     constexpr u32 RY = SYM_THREADS / SYM_T;   // rows per sweep
     const u32 x = threadIdx.x % SYM_T, y0 = threadIdx.x / SYM_T;
@@ -378,10 +391,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         int grid = ws.sms * 8;
         if (grid > (int)n)
             grid = (int)n;
-        auto kr = dt == 0   ? k_rowmin<0, false>
-                  : dt == 1 ? k_rowmin<1, false>
-                  : dt == 2 ? k_rowmin<2, false>
-                            : k_rowmin<3, false>;
+        auto kr = dt == 0 ? k_rowmin<0> : dt == 1 ? k_rowmin<1> : dt == 2 ? k_rowmin<2> : k_rowmin<3>;
         kr<<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
         if ((err = cudaGetLastError()) != cudaSuccess)
             return err;
@@ -411,7 +421,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
     auto k0b = pick0(std::false_type{});
     auto k1 = k_contract<0, 0, false, false, true>;
     if ((err = set_smem(k0a, smem2)) != cudaSuccess || (err = set_smem(k0b, smem)) != cudaSuccess ||
-        (err = set_smem(k1, smem2)) != cudaSuccess || (err = set_smem(k_sym_c1, sym_smem_bytes())) != cudaSuccess)
+        (err = set_smem(k1, smem2)) != cudaSuccess || (err = set_smem(k_sym, sym_smem_bytes())) != cudaSuccess)
         return err;
     for (int r = 0; r < ws.levels; ++r) {
         StepArgs sa;
@@ -483,9 +493,17 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         } else {
             k1<<<2 * ws.contract_blocks, CONTRACT_THREADS2, smem2, s>>>(ca, 0u, 0xFFFFFFFFu);
         }
-        if (r == 0 && vec) {
+        if (vec && r == 0) {
+            // C_1's row minima also take P's column minima
             prof_launches(1);
-            k_sym_c1<<<ws.sms * 3, SYM_THREADS, sym_smem_bytes(), s>>>(cb[0], ws.ctr, ws.best[1]);
+            const u32 g = (u32)((h + CMIN_THREADS - 1) / CMIN_THREADS);
+            const u32 gy = (u32)((h + CMIN_ROWS - 1) / CMIN_ROWS);
+            k_colmin_p<<<dim3(g, gy), CMIN_THREADS, 0, s>>>(cb[0], ws.ctr, ws.best[1]);
+        }
+        if (vec && r == 1) {
+            // level 1 contracted the unsymmetrized P: symmetrize C_2
+            prof_launches(1);
+            k_sym<<<ws.sms * 3, SYM_THREADS, sym_smem_bytes(), s>>>(cb[1], ws.ctr, 1, ws.best[0]);
         }
         prof_end(ph, s);
         if ((err = cudaGetLastError()) != cudaSuccess)
