@@ -12,7 +12,7 @@
 namespace appd {
 
 constexpr int MAX_LEVELS = 20;     // Boruvka levels: ceil(log2 65536) = 16, plus slack
-constexpr int CONTRACT_ROWS = 8;   // rows of the current matrix per contraction work item
+constexpr int CONTRACT_ROWS = 16;  // rows of the current matrix per contraction work item
 constexpr int CONTRACT_THREADS = 1024;   // one contraction CTA per SM
 constexpr int CONTRACT_THREADS2 = 512;   // two per SM (half the bins each)
 
