@@ -23,14 +23,17 @@
 
 namespace appd {
 
+// rows_per_cta rows of one column block per CTA, in batches of rows_cap
+// (the column block's sort and table are built once per CTA)
+constexpr u32 FILL_ROWS_MAX = 8192;
+
 template <int DT>
 __global__ void __launch_bounds__(FT, 2) k_fill(const u32* __restrict__ pos, const u32* __restrict__ st,
-                                                u32 n, u32 rows_per_cta, u32* __restrict__ M)
+                                                u32 n, u32 rows_per_cta, u32 rows_cap, u32* __restrict__ M)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const u32 r0 = blockIdx.y * rows_per_cta;
-    fill_tile<DT>(pos, st, n, blockIdx.x * FC, r0, min(rows_per_cta, n - r0), rows_per_cta, M,
-                  smem_raw);
+    fill_tile<DT>(pos, st, n, blockIdx.x * FC, r0, min(rows_per_cta, n - r0), rows_cap, M, smem_raw);
 }
 
 // ----------------------------------------------------- Algorithm 4 form
@@ -116,21 +119,23 @@ cudaError_t run_fill(Workspace& ws, int dt, void* M, cudaStream_t s)
     if (n == 1)
         return cudaMemsetAsync(M, 0, sizeof(u32), s);
     const u32 gx = (n + FC - 1) / FC;
-    // rows per CTA: enough CTAs for several waves, at most 1024 rows
+    // rows per CTA: enough CTAs for several waves, at most FILL_ROWS_MAX rows
+    // (handled in batches of at most 1024, so the shared memory stays small)
     u64 target = (u64)ws.sms * 2 * 4;
     u32 rows = (u32)(((u64)n * gx + target - 1) / target);
     if (rows < 32)
         rows = 32;
-    if (rows > 1024)
-        rows = 1024;
+    if (rows > FILL_ROWS_MAX)
+        rows = FILL_ROWS_MAX;
+    const u32 cap = rows < 1024 ? rows : 1024;
     dim3 grid(gx, (n + rows - 1) / rows);
-    const size_t smem = fill_smem_bytes(rows);
+    const size_t smem = fill_smem_bytes(cap);
     cudaError_t e;
     auto kf = dt == 0 ? k_fill<0> : dt == 1 ? k_fill<1> : dt == 2 ? k_fill<2> : k_fill<3>;
     if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)fill_smem_bytes(1024))) != cudaSuccess)
         return e;
-    kf<<<grid, FT, smem, s>>>(ws.pos, ws.st, n, rows, (u32*)M);
+    kf<<<grid, FT, smem, s>>>(ws.pos, ws.st, n, rows, cap, (u32*)M);
     return cudaGetLastError();
 }
 
