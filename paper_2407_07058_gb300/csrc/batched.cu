@@ -53,7 +53,7 @@ struct BatchArgs {
     u32* status;
     u32 bin_cap;          // u64 bins that fit the dynamic shared memory
     u32 warp_bins;        // u64 bins per warp when each warp owns a group
-    u32 fill_rows;        // rows per fill tile
+    u32 fill_rows;        // rows per fill batch (shared memory of a fill tile)
     u32* posst;           // leaf positions and sparse tables of all graphs
     const u64* pst_off;   // graph g's pos at posst + pst_off[g], its table after n entries
     u64* best0;           // round-1 minima of all graphs (k_rowmin_batched)
@@ -546,7 +546,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
 }
 
 // The fill of every graph of a batch: one CTA per tile (graph, 128 columns,
-// up to fill_rows rows), from the tile list built with the batch layout.
+// all rows in batches of fill_rows), from the tile list built with the batch
+// layout.
 // All CTAs of the GPU share the work, at the occupancy of the single-solve
 // fill, instead of one CTA filling a whole graph.
 constexpr int FILLB_THREADS = 256;
@@ -689,7 +690,7 @@ DescLayout desc_layout(const BatchDesc& d, u32 fill_rows)
     L.posst_words = L.rows = 0;
     for (u32 n : d.n) {
         if (n >= 2) {
-            L.ntiles += ((n + FC - 1) / FC) * ((n + fill_rows - 1) / fill_rows);
+            L.ntiles += (n + FC - 1) / FC;
             L.ntasks += (n + ROWB_ROWS - 1) / ROWB_ROWS;
         }
         L.posst_words += (size_t)n * (1 + st_levels_of(n));
@@ -731,9 +732,10 @@ void fill_desc(const BatchDesc& d, u32 fill_rows, const DescLayout& L, std::vect
             continue;
         for (u32 r0 = 0; r0 < n; r0 += ROWB_ROWS)
             tasks.push_back(make_uint2(g, r0));
+        // a tile is a whole column block: its sort and table are built once,
+        // the rows follow in batches of fill_rows
         for (u32 j0 = 0; j0 < n; j0 += FC)
-            for (u32 r0 = 0; r0 < n; r0 += fill_rows)
-                tiles.push_back(make_uint4(g, j0, r0, std::min(fill_rows, n - r0)));
+            tiles.push_back(make_uint4(g, j0, 0u, n));
     }
     for (u32 g = 0; g < cnt; ++g) {
         pst[g] = acc;

@@ -54,12 +54,12 @@ __global__ void __launch_bounds__(256) k_rowmin(const u32* __restrict__ W, u32 n
 
 // Round 1 over the upper triangle only (K1, symmetric form).  W is
 // symmetric, so element (i, j), i < j, is both a candidate for row i and for
-// row j.  A CTA owns 128 rows x 1024 columns; each warp a 128-column slab.
+// row j.  A CTA owns 256 rows x 1024 columns; each warp a 128-column slab.
 // Lanes own 4 columns: their column minima over the CTA's rows give row j's
 // candidates from rows i < j; per-row minima are warp reductions
 // (redux.sync) merged across warps in shared memory.  Both go to best[] with 64-bit atomic minima on packed edges, so
 // every unordered pair is read once (half of W).  best[] starts at +inf.
-constexpr u32 RS_ROWS = 128, RS_COLS = 1024;
+constexpr u32 RS_ROWS = 256, RS_COLS = 1024;
 
 template <int DT>
 __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u32 n,
