@@ -232,25 +232,33 @@ __device__ __forceinline__ void sort_rows4(u32* rid, u32 np)
             rid[q] = rid[0];
 }
 
-// One contraction level with one warp per group: warp w folds every row of
-// group A (A = w, w + warps, ...) into its own cn bins in shared memory, then
-// writes row A of C_{r+1} (row stride sout) and A's row minimum.  Groups
-// proceed concurrently and independently (no block barrier between groups),
-// so 16 groups' loads are in flight instead of one item's.  Level 0 reads W
-// rows at any alignment (load_groups); later levels read C_r with row stride
-// sin.  Needs cn <= the per-warp capacity.
+// One contraction level with one warp per group: a warp claims a group A,
+// folds every row of A into its own cn bins in shared memory, writes row A
+// of C_{r+1} (row stride sout) and A's row minimum, and claims the next.
+// Groups proceed concurrently and independently (no block barrier between
+// groups), so 16 groups' loads are in flight instead of one item's.  Level 0
+// reads W rows at any alignment (load_groups); later levels read C_r with
+// row stride sin.  Needs cn <= the per-warp capacity.
 template <int DT, int LEVEL0>
 __device__ void contract_level_warps(const ContractArgs& a, u32 cr, u32 cn, u32 sin, u32 sout,
-                                     const u32* wlo, const u32* whi, u64* wbins, u32 wcap)
+                                     const u32* wlo, const u32* whi, u64* wbins, u32 wcap, u32* gnext)
 {
-    const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     u64* bins = wbins + (size_t)wid * wcap;
     // bins start empty once per level; each group's write-out empties them
     // again for the warp's next group
     for (u32 b = lane; b < cn; b += 32)
         bins[b] = EDGE_INF;
     __syncwarp();
-    for (u32 A = wid; A < cn; A += nw) {
+    // groups are claimed one at a time (sizes vary), so no warp idles behind
+    // a statically assigned share; *gnext starts at 0 (the caller resets it)
+    for (;;) {
+        u32 A = 0;
+        if (lane == 0)
+            A = atomicAdd(gnext, 1u);
+        A = __shfl_sync(0xFFFFFFFFu, A, 0);
+        if (A >= cn)
+            break;
         const u32 m0 = a.gstart[A], m1 = a.gstart[A + 1];
         for (u32 p = m0; p < m1; p += 4) {
             const u32 np = min(4u, m1 - p);
@@ -444,11 +452,16 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, u32* po
         const u32 cr = ((volatile u32*)ctr->c)[r], cn = ((volatile u32*)ctr->c)[r + 1];
         u64* bins = reinterpret_cast<u64*>(smem);
         if (cn <= b.warp_bins) {
+            __shared__ u32 s_gnext;   // next group to claim
+            if (threadIdx.x == 0)
+                s_gnext = 0;
+            __syncthreads();
             const u32 sout = ((cn & 1u) && (size_t)cn * (cn + 1) <= cap_half[r & 1]) ? cn + 1 : cn;
             if (r == 0)
-                contract_level_warps<DT, 1>(ca, cr, cn, stride, sout, W, W + (size_t)n * n, bins, b.warp_bins);
+                contract_level_warps<DT, 1>(ca, cr, cn, stride, sout, W, W + (size_t)n * n, bins, b.warp_bins,
+                                            &s_gnext);
             else
-                contract_level_warps<DT, 0>(ca, cr, cn, stride, sout, W, W, bins, b.warp_bins);
+                contract_level_warps<DT, 0>(ca, cr, cn, stride, sout, W, W, bins, b.warp_bins, &s_gnext);
             stride = sout;
             __syncthreads();
             continue;
