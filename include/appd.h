@@ -16,7 +16,7 @@
  *  - Ordering: U32 weights compare as unsigned integers; F32 weights compare
  *    by IEEE-754 totalOrder (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN).
  *    Ties are broken by the edge's endpoint pair, so results never depend on
- *    tie-breaking (Section 5 notes ties do not matter).
+ *    tie-breaking (Section 5 notes that the tie order is irrelevant).
  *  - Output: every off-diagonal M(i,j) is the bit pattern of one input weight
  *    (the largest edge on a minimax path); the diagonal M(i,i) is all-zero
  *    bits.  W(i,i) is never read.  Results are exact (bit-identical to the

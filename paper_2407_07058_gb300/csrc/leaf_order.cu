@@ -2,7 +2,7 @@
 //
 // Section 3 notes that the APPD matrix can also be produced by adding the MST
 // edges from small to large (a single-linkage dendrogram), and Section 7
-// quotes that the distances can be read off the dendrogram.  We need, for the
+// notes that the distances follow from the dendrogram.  We need, for the
 // fill, a leaf order pos[] and gaps gap[k] (merge height between the leaves
 // at positions k and k+1) such that
 //     key(M(i,j)) = max gap[min(pos_i,pos_j) .. max(pos_i,pos_j) - 1].
