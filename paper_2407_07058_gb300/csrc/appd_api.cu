@@ -131,6 +131,7 @@ cudaError_t appd::workspace_create(int64_t n, Workspace** out)
     nw->contract_blocks = nw->sms;
     nw->bin_cap = (u32)((smem_optin - 2048) / 8);
     nw->bin_cap2 = (u32)((smem_optin / 2 - 2048) / 8);
+    nw->bin_cap_t = contract_tma_bin_cap(smem_optin);
     *out = nw;
     return cudaSuccess;
 }

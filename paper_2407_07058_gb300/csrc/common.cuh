@@ -162,8 +162,27 @@ __device__ __forceinline__ u32 block_excl_scan(u32 v, u32* total, u32* sh)
 struct GridBar {
     u32 count;
     u32 abort;
-    u32 gen;     // unused (layout kept for the host's memset of count + abort)
+    u32 failed;  // set when a wait of the current solve ran out or its state
+                 // was found inconsistent; cleared at the start of each solve
+                 // (the host's memset before a launch clears count + abort only)
 };
+
+// Records a failure of the current solve: in the device status word (read
+// and cleared by the host) and in the solve's own flag, which the later
+// phases of the same solve test before they follow any index derived from
+// the spanning tree.
+__device__ __forceinline__ void record_failure(u32* status, u32* failed, u32 code)
+{
+    if (status)
+        atomicOr(status, code);
+    if (failed)
+        atomicExch(failed, 1u);
+}
+
+__device__ __forceinline__ bool solve_failed(const GridBar* bar)
+{
+    return *(const volatile u32*)&bar->failed != 0u;
+}
 
 __device__ __forceinline__ u32 atom_add_release(u32* p, u32 v)
 {
@@ -193,7 +212,7 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, u32* status,
                 __nanosleep(32);
                 if (globaltimer_ns() - t0 > limit_ns) {
                     atomicExch(&bar->abort, 1u);
-                    atomicOr(status, DEV_TIMEOUT);
+                    record_failure(status, &bar->failed, DEV_TIMEOUT);
                     ok = 0;
                     break;
                 }

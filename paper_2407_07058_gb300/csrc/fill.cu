@@ -29,9 +29,12 @@ constexpr u32 FILL_ROWS_MAX = 8192;
 
 template <int DT>
 __global__ void __launch_bounds__(FT, 2) k_fill(const u32* __restrict__ pos, const u32* __restrict__ st,
-                                                u32 n, u32 rows_per_cta, u32 rows_cap, u32* __restrict__ M)
+                                                u32 n, u32 rows_per_cta, u32 rows_cap, u32* __restrict__ M,
+                                                const Counters* __restrict__ ctr)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (solve_failed(&ctr->bar))   // no valid leaf order: leave M unwritten
+        return;
     const u32 r0 = blockIdx.y * rows_per_cta;
     fill_tile<DT>(pos, st, n, blockIdx.x * FC, r0, min(rows_per_cta, n - r0), rows_cap, M, smem_raw);
 }
@@ -41,8 +44,11 @@ constexpr int A4_TR = 8;     // tree1 positions per tile
 constexpr int A4_TC = 256;   // tree2 positions per tile
 
 __global__ void k_a4_count(const u32* __restrict__ pos, const u32* __restrict__ nha,
-                           const u32* __restrict__ nsize, u32 n, u32* __restrict__ tiles)
+                           const u32* __restrict__ nsize, u32 n, u32* __restrict__ tiles,
+                           const Counters* __restrict__ ctr)
 {
+    if (solve_failed(&ctr->bar))   // no valid leaf order: leave M unwritten
+        return;
     for (u32 y = blockIdx.x * blockDim.x + threadIdx.x + 1; y < n; y += gridDim.x * blockDim.x) {
         u32 rows = pos[y] - pos[nha[y]];
         u32 cols = nsize[y];
@@ -70,6 +76,8 @@ __global__ void __launch_bounds__(256) k_a4_fill(const u32* __restrict__ pos, co
                                                  u32* __restrict__ M)
 {
     __shared__ u32 s_e;
+    if (solve_failed(&ctr->bar))
+        return;
     const u32 total = ctr->fill_total, m = n - 1;
     for (u32 tile = blockIdx.x; tile < total; tile += gridDim.x) {
         if (threadIdx.x == 0) {
@@ -135,7 +143,7 @@ cudaError_t run_fill(Workspace& ws, int dt, void* M, cudaStream_t s)
     if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)fill_smem_bytes(1024))) != cudaSuccess)
         return e;
-    kf<<<grid, FT, smem, s>>>(ws.pos, ws.st, n, rows, cap, (u32*)M);
+    kf<<<grid, FT, smem, s>>>(ws.pos, ws.st, n, rows, cap, (u32*)M, ws.ctr);
     return cudaGetLastError();
 }
 
@@ -146,7 +154,7 @@ cudaError_t run_fill_alg4(Workspace& ws, int dt, void* M, u32* status, cudaStrea
     if (n == 1)
         return cudaMemsetAsync(M, 0, sizeof(u32), s);
     const u32 m = n - 1;
-    k_a4_count<<<(m + 255) / 256, 256, 0, s>>>(ws.pos, ws.nha, ws.nsize, n, ws.a4_start);
+    k_a4_count<<<(m + 255) / 256, 256, 0, s>>>(ws.pos, ws.nha, ws.nsize, n, ws.a4_start, ws.ctr);
     k_a4_scan<<<1, 1024, 0, s>>>(ws.a4_start, m, ws.ctr);
     k_diag_zero<<<(n + 255) / 256, 256, 0, s>>>((u32*)M, n);
     const int grid = ws.sms * 8;

@@ -44,6 +44,7 @@ struct Workspace {
     int contract_blocks = 0;
     u32 bin_cap = 0;         // u64 bins per contraction CTA (one CTA per SM)
     u32 bin_cap2 = 0;        // u64 bins per contraction CTA (two CTAs per SM)
+    u32 bin_cap_t = 0;       // u64 bins beside the copy ring of the bulk-copy contraction
     void* base = nullptr;
     size_t bytes = 0;
 
@@ -88,6 +89,13 @@ cudaError_t run_fill_alg4(Workspace& ws, int dt, void* M, u32* status, cudaStrea
 cudaError_t run_insert(const void* M, int64_t n, int dt, const void* w, void* Mo, u32* d, int sms,
                        cudaStream_t s);
 cudaError_t run_fill_trivial(int64_t n, void* M, cudaStream_t s);   // n == 1
+// level-0 contraction over the upper triangle fed by bulk copies
+// (contract_tma.cu); runs when |C_1| <= run_max, needs n % 4 == 0 and W and
+// ca.label 16-byte aligned; ca.bin_cap <= contract_tma_bin_cap(smem_optin)
+struct ContractArgs;
+u32 contract_tma_bin_cap(int smem_optin);
+cudaError_t launch_contract0_tma(const ContractArgs& ca, int dt, int blocks, u32 run_max, u32* status,
+                                 cudaStream_t s);
 
 // profiling (appd_profile_begin/end): phases of a solve
 enum Phase { PH_ROWMIN = 0, PH_STEP, PH_CONTRACT0, PH_CONTRACT, PH_LEAF, PH_FILL, PH_BATCHED, PH_COUNT };

@@ -74,6 +74,9 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
 {
     const u32 n = a.n, m = n - 1, na = 2 * m;
     const u32 me = t.rank(), ts = t.size();
+    // an earlier phase of this solve failed: the tree may be incomplete
+    if (solve_failed(&a.ctr->bar))
+        return;
     __shared__ u32 s_cnt[256];
     __shared__ u32 s_off[256];
     __shared__ u32 s_wc[SORT_NW][256];
@@ -301,7 +304,7 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
         } else {
             u32 sd = suf[2 * v];
             if (sd < 1 || sd > n - 1) {   // not a tree: report, never write out of range
-                atomicOr(a.status, DEV_INTERNAL);
+                record_failure(a.status, &a.ctr->bar.failed, DEV_INTERNAL);
                 continue;
             }
             u32 p = n - sd;

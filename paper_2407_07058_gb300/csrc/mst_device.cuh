@@ -43,10 +43,10 @@ __device__ void step_body(const Team& t, const StepArgs& a)
         if (e != EDGE_INF && edge_lo(e) < a.n && edge_hi(e) < a.n) {
             u32 ca = a.comp[edge_lo(e)], cb = a.comp[edge_hi(e)];
             if (ca != x && cb != x)
-                atomicOr(a.status, DEV_INTERNAL);
+                record_failure(a.status, &ctr->bar.failed, DEV_INTERNAL);
             h = (ca == x) ? cb : ca;
         } else {
-            atomicOr(a.status, DEV_INTERNAL);
+            record_failure(a.status, &ctr->bar.failed, DEV_INTERNAL);
         }
         a.hook[x] = h < c ? h : x;
         a.cnt[x] = 0;
@@ -83,7 +83,7 @@ __device__ void step_body(const Team& t, const StepArgs& a)
         if (fl[it % 3] == 0)
             break;
         if (it == 63 && me == 0)
-            atomicOr(a.status, DEV_INTERNAL);
+            record_failure(a.status, &ctr->bar.failed, DEV_INTERNAL);
     }
     for (u32 x = me; x < c; x += ts)
         a.flag[x] = (a.par[x] == x) ? 1u : 0u;

@@ -346,6 +346,7 @@ __global__ void k_mst_init(Counters* ctr, u32* comp, u32 n, u32 bar_reset)
             ctr->bar.count = 0;
             ctr->bar.abort = 0;
         }
+        ctr->bar.failed = 0;
     }
 }
 
@@ -486,7 +487,17 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         prof_begin(ph, s);
         ContractArgs ca1 = ca;
         ca.bin_cap = ws.bin_cap2;
-        if (r == 0) {
+        if (r == 0 && vec && ws.bin_cap_t > 0) {
+            // upper triangle streamed by bulk copies while |C_1| fits beside
+            // the copy ring, else one CTA per SM with all bins
+            ContractArgs cat = ca;
+            cat.bin_cap = ws.bin_cap_t;
+            if ((err = launch_contract0_tma(cat, dt, ws.contract_blocks, ws.bin_cap_t, status, s)) !=
+                cudaSuccess)
+                return err;
+            k0b<<<ws.contract_blocks, CONTRACT_THREADS, smem, s>>>(ca1, ws.bin_cap_t + 1, 0xFFFFFFFFu);
+            prof_launches(1);
+        } else if (r == 0) {
             k0a<<<2 * ws.contract_blocks, CONTRACT_THREADS2, smem2, s>>>(ca, 0u, ws.bin_cap2);
             k0b<<<ws.contract_blocks, CONTRACT_THREADS, smem, s>>>(ca1, ws.bin_cap2 + 1, 0xFFFFFFFFu);
             prof_launches(1);
