@@ -82,6 +82,7 @@ size_t appd::workspace_layout(Workspace& w, char* base, int64_t cap)
     w.chunk_start = (u32*)take((N + 4) * sizeof(u32));
     w.adj_off = (u32*)take((N + 4) * sizeof(u32));
     w.a4_start = (u32*)take((N + 4) * sizeof(u32));
+    w.label16 = (unsigned short*)take((N + 8) * sizeof(unsigned short));
     w.mst = (u64*)take((N + 1) * 8);
     w.adj = (u32*)take(2 * N * sizeof(u32));
     w.aslot = (u32*)take(2 * N * sizeof(u32));

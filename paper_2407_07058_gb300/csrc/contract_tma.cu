@@ -10,21 +10,24 @@
 // become row A of P and their minimum the row's candidate best edge.
 //
 // One CTA per SM with two roles:
-//   * a producer thread claims items, and for every column chunk of
-//     TC_CH columns and every pass of up to TC_ROWS rows issues one bulk copy
-//     per row segment right of that row's diagonal (plus the chunk's labels
-//     on the last pass) into the next free ring stage, completing on the
-//     stage's "full" mbarrier;
-//   * TC_CONS consumer threads own one 4-column group of each chunk each,
-//     keep the running minimum of their 4 columns across the passes of a
-//     chunk in registers, and fold into the bins once per chunk (not once
-//     per pass), then release the stage on its "empty" mbarrier.
-// At the end of an item the consumers write the bins out and reset them
-// while the producer already streams the next item's rows.
+//   * a producer warp claims items and, for every chunk of TC_CH columns and
+//     every row of the item that reaches the chunk (rows ascending), issues
+//     one bulk copy of that row's segment right of its diagonal into the
+//     next free ring stage (plus the chunk's 16-bit labels with the chunk's
+//     last row), completing on the stage's "full" mbarrier;
+//   * TC_CONS consumer threads own TC_G interleaved 4-column groups of every
+//     chunk, keep the running minimum of their columns over the chunk's rows
+//     in registers and fold them into the bins once per chunk, then release
+//     the stage on its "empty" mbarrier.
+// One row per stage keeps the stages full (a component's rows are spread
+// over the matrix, so few of them reach the left part of a row range) and
+// gives each consumer 16 columns per stage to amortize the stage's fixed
+// work.  At the end of an item the consumers write the bins out and reset
+// them while the producer already streams the next item.
 //
 // Every wait is bounded (BARRIER_TIMEOUT_NS): a wait that runs out sets the
-// CTA's abort flag and DEV_TIMEOUT in the status word, every role leaves
-// its loop, and the producer waits (again bounded) for the copies it issued
+// CTA's abort flag, records DEV_TIMEOUT for the solve, every role leaves its
+// loop, and the producer waits (again bounded) for the copies it issued
 // before the CTA exits.
 #include "internal.h"
 #include "mst_device.cuh"
@@ -36,22 +39,24 @@ namespace {
 constexpr int TC_CONS_WARPS = 16;
 constexpr u32 TC_CONS = TC_CONS_WARPS * 32;     // consumer threads
 constexpr u32 TC_THREADS = TC_CONS + 32;        // plus one producer warp
-constexpr u32 TC_CH = 4 * TC_CONS;              // columns per chunk: one group per consumer
-constexpr u32 TC_ROWS = 4;                      // rows per stage (one pass)
+constexpr u32 TC_G = 4;                         // 4-column groups per consumer and chunk
+constexpr u32 TC_CH = 4 * TC_CONS * TC_G;       // columns per chunk
 constexpr u32 TC_STAGES = 3;
 constexpr u32 TC_ROW_BYTES = TC_CH * 4;
-constexpr u32 TC_STAGE_BYTES = (TC_ROWS + 1) * TC_ROW_BYTES;   // rows, then the chunk's labels
+// the chunk's labels, copied from a multiple of 8 columns (16-byte rule)
+constexpr u32 TC_LAB_BYTES = (TC_CH + 8) * 2;
+constexpr u32 TC_STAGE_BYTES = TC_ROW_BYTES + TC_LAB_BYTES;
 constexpr u32 TC_RING_BYTES = TC_STAGES * TC_STAGE_BYTES;
+static_assert(TC_STAGE_BYTES % 16 == 0, "stages start 16-byte aligned");
 
 enum : u32 { TF_FIRST = 1, TF_LAST = 2, TF_END_ITEM = 4, TF_END = 8 };
 
-// what the producer tells the consumers about one stage
+// what the producer tells the consumers about one stage (three 16-byte words)
 struct __align__(16) TcMeta {
-    u32 c0, c1;            // columns [c0, c1) of the chunk
-    u32 np, flags;         // rows of this pass; TF_* bits
-    u32 rid[TC_ROWS];      // the pass's rows, ascending
-    u32 A, b0, nb, single;       // the item: group, bin range, one-chunk group
-    u32 r0, pad[3];              // the item's smallest row
+    u32 c0, c1, row, flags;        // columns [c0, c1) of the chunk; the stage's row; TF_* bits
+    u32 A, b0, nb, single;         // the item: group, bin range, one-chunk group
+    u32 r0, cl0, pad0, pad1;       // the item's smallest row; first column of the labels
+    u32 pad2[4];
 };
 
 __device__ __forceinline__ u32 smem_addr(const void* p) { return (u32)__cvta_generic_to_shared(p); }
@@ -165,18 +170,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const u32 total = total_chunks * nbr;
     const u32* W = (const u32*)a.cin;
     const u32 lane = tid & 31, warp = tid >> 5;
+    u32* failed = &ctr->bar.failed;
 
     if (warp == TC_CONS_WARPS) {
         // ------------------------------------------------- producer warp
-        // Lane q holds the item's row of rank q; per stage, the lanes of
-        // the pass issue one row copy each and lane 0 publishes the stage.
+        // Lane q holds the item's row of rank q; lane 0 publishes every
+        // stage and issues its copies.
         constexpr u32 FULL = 0xFFFFFFFFu;
         u32 it = 0;
         bool ok = true;
         // every lane waits for stage slot it % TC_STAGES to be free
         auto take_slot = [&](u32& slot) -> bool {
             slot = it % TC_STAGES;
-            return __all_sync(FULL, tc_wait(&s_empty[slot], ((it / TC_STAGES) & 1u) ^ 1u, &s_abort, status, &ctr->bar.failed));
+            return __all_sync(FULL, tc_wait(&s_empty[slot], ((it / TC_STAGES) & 1u) ^ 1u, &s_abort, status, failed));
         };
         for (;;) {
             u32 item = 0;
@@ -213,44 +219,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const u32 cstart = d0 < cr ? d0 : cr;
             for (u32 c0 = cstart;;) {
                 const u32 c1 = min(cr, c0 + TC_CH);
-                for (u32 p0 = 0;; p0 += TC_ROWS) {
-                    const u32 np = c0 < c1 ? min(TC_ROWS, nrows - p0) : 0u;
-                    const u32 next_col = __shfl_sync(FULL, mycol, (p0 + TC_ROWS) & 31u);
-                    const bool more = p0 + TC_ROWS < nrows && next_col < c1;
-                    const u32 flags = (p0 == 0 ? TF_FIRST : 0u) | (more ? 0u : TF_LAST) |
+                for (u32 q = 0;; ++q) {
+                    // row q reaches this chunk (q == 0 always does)
+                    const u32 row = __shfl_sync(FULL, myrow, q & 31u);
+                    const u32 dq = __shfl_sync(FULL, mycol, q & 31u);
+                    const u32 next_col = __shfl_sync(FULL, mycol, (q + 1) & 31u);
+                    const bool more = q + 1 < nrows && next_col < c1;
+                    const u32 flags = (q == 0 ? TF_FIRST : 0u) | (more ? 0u : TF_LAST) |
                                       (!more && c1 == cr ? TF_END_ITEM : 0u);
-                    const u32 q = lane - p0;   // this lane's row within the pass
-                    const bool mine = lane >= p0 && q < np;
-                    const u32 s0 = max(c0, mycol);
-                    const u32 bytes = (mine && s0 < c1) ? (c1 - s0) * 4u : 0u;
+                    const u32 s0 = max(c0, dq);
+                    const u32 rbytes = s0 < c1 ? (c1 - s0) * 4u : 0u;
                     const bool lab = !more && c0 < c1;
-                    const u32 tx = __reduce_add_sync(FULL, bytes) + (lab ? (c1 - c0) * 4u : 0u);
-                    // the pass's rows for the consumers (rows past np repeat row p0)
-                    u32 rq[TC_ROWS];
-#pragma unroll
-                    for (u32 i = 0; i < TC_ROWS; ++i)
-                        rq[i] = __shfl_sync(FULL, myrow, (p0 + (i < np ? i : 0u)) & 31u);
+                    const u32 cl0 = c0 & ~7u, cl1 = (c1 + 7u) & ~7u;
+                    const u32 lbytes = lab ? (cl1 - cl0) * 2u : 0u;
                     u32 slot;
                     if (!(ok = take_slot(slot)))
                         break;
-                    unsigned char* st = ring + slot * TC_STAGE_BYTES;
                     if (lane == 0) {
+                        unsigned char* st = ring + slot * TC_STAGE_BYTES;
                         uint4* mw = reinterpret_cast<uint4*>(&s_meta[slot]);
-                        mw[0] = make_uint4(c0, c1, np, flags);
-                        mw[1] = make_uint4(rq[0], rq[1], rq[2], rq[3]);
-                        mw[2] = make_uint4(A, b0, nb, single);
-                        mw[3] = make_uint4(r0, 0u, 0u, 0u);
-                        if (tx == 0)
+                        mw[0] = make_uint4(c0, c1, row, flags);
+                        mw[1] = make_uint4(A, b0, nb, single);
+                        mw[2] = make_uint4(r0, cl0, 0u, 0u);
+                        if (rbytes + lbytes == 0) {
                             mbar_arrive(&s_full[slot]);
-                        else
-                            mbar_arrive_tx(&s_full[slot], tx);
+                        } else {
+                            mbar_arrive_tx(&s_full[slot], rbytes + lbytes);
+                            if (rbytes)
+                                bulk_load(st + (s0 - c0) * 4u, W + (size_t)row * cr + s0, rbytes, &s_full[slot]);
+                            if (lbytes)
+                                bulk_load(st + TC_ROW_BYTES, a.label16 + cl0, lbytes, &s_full[slot]);
+                        }
                     }
                     __syncwarp();
-                    if (bytes)
-                        bulk_load(st + q * TC_ROW_BYTES + (s0 - c0) * 4u, W + (size_t)myrow * cr + s0, bytes,
-                                  &s_full[slot]);
-                    if (lab && lane == 31)
-                        bulk_load(st + TC_ROWS * TC_ROW_BYTES, a.label + c0, (c1 - c0) * 4u, &s_full[slot]);
                     ++it;
                     if (!more)
                         break;
@@ -282,98 +283,103 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const u32 lo = end_sent ? (it + 1 > TC_STAGES ? it + 1 - TC_STAGES : 0u)
                                 : (it > TC_STAGES ? it - TC_STAGES : 0u);
         for (u32 i = lo; i < it; ++i)
-            tc_wait(&s_full[i % TC_STAGES], (i / TC_STAGES) & 1u, &s_abort, status, &ctr->bar.failed, false);
+            tc_wait(&s_full[i % TC_STAGES], (i / TC_STAGES) & 1u, &s_abort, status, failed, false);
         return;
     }
 
     // ----------------------------------------------------------- consumers
+    // group t of this thread: columns c0 + 4 * ctid + 4 * TC_CONS * t .. +3
+    // (interleaved, so a warp's 16-byte shared loads are contiguous)
     const u32 ctid = tid;   // 0 .. TC_CONS-1
     u32 it = 0, cph = 0;
-    u32 bk[4] = {0, 0, 0, 0}, bi[4] = {0, 0, 0, 0};
+    u32 bk[4 * TC_G], bi[4 * TC_G];
+#pragma unroll
+    for (u32 i = 0; i < 4 * TC_G; ++i)
+        bk[i] = bi[i] = 0u;
     // all consumer warps meet (bounded); false once any wait ran out
     auto cons_sync = [&]() -> bool {
         __syncwarp();
         if (lane == 0)
             mbar_arrive(&s_cbar);
-        const bool okw = tc_wait(&s_cbar, cph, &s_abort, status, &ctr->bar.failed);
+        const bool okw = tc_wait(&s_cbar, cph, &s_abort, status, failed);
         cph ^= 1u;
         return __all_sync(0xFFFFFFFFu, okw);
     };
     for (;;) {
         const u32 slot = it % TC_STAGES;
-        if (!__all_sync(0xFFFFFFFFu, tc_wait(&s_full[slot], (it / TC_STAGES) & 1u, &s_abort, status, &ctr->bar.failed)))
+        if (!__all_sync(0xFFFFFFFFu, tc_wait(&s_full[slot], (it / TC_STAGES) & 1u, &s_abort, status, failed)))
             break;
         const uint4* mr = reinterpret_cast<const uint4*>(&s_meta[slot]);
-        const uint4 m0 = mr[0];
-        const u32 flags = m0.w;
+        const uint4 w0 = mr[0];
+        const u32 flags = w0.w;
         if (flags & TF_END)
             break;
-        const uint4 m1 = mr[1], m2 = mr[2], m3 = mr[3];
-        const u32 c0 = m0.x, c1 = m0.y, np = m0.z;
-        const u32 A = m2.x, b0 = m2.y, nb = m2.z, single = m2.w, r0 = m3.x;
-        const u32 rid[TC_ROWS] = {m1.x, m1.y, m1.z, m1.w};
-        const u32 j = c0 + 4u * ctid;
+        const uint4 w1 = mr[1], w2 = mr[2];
+        const u32 c0 = w0.x, c1 = w0.y, row = w0.z;
+        const u32 A = w1.x, b0 = w1.y, nb = w1.z, single = w1.w, r0 = w2.x, cl0 = w2.y;
         const unsigned char* st = ring + slot * TC_STAGE_BYTES;
-        if (j < c1 && np > 0) {
-            // all four row slots at once (slots past np hold stale data and
-            // are not used), then the running minima
-            const uint4* rows = reinterpret_cast<const uint4*>(st);
-            uint4 v[TC_ROWS];
+        const uint4* rows = reinterpret_cast<const uint4*>(st);
+        // all groups' 16 bytes at once; groups left of the row's segment
+        // hold stale data and are not used
+        uint4 v[TC_G];
 #pragma unroll
-            for (int q = 0; q < (int)TC_ROWS; ++q)
-                v[q] = rows[q * (TC_CH / 4) + ctid];
-            const bool first = (flags & TF_FIRST) != 0;
+        for (u32 t = 0; t < TC_G; ++t)
+            v[t] = rows[ctid + TC_CONS * t];
+        const bool first = (flags & TF_FIRST) != 0;
+#pragma unroll
+        for (u32 t = 0; t < TC_G; ++t) {
+            const u32 j = c0 + 4u * (ctid + TC_CONS * t);
+            if (j >= c1)
+                continue;
             if (first) {
                 // the item's smallest row reaches every group of the chunk
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    bk[c] = key_of(lane_of_dyn(v[0], c), DT);
-                    bi[c] = rid[0];
+                    bk[4 * t + c] = key_of(lane_of_dyn(v[t], c), DT);
+                    bi[4 * t + c] = row;
                 }
-            }
-            const u32 rmax = np == 1 ? rid[0] : np == 2 ? rid[1] : np == 3 ? rid[2] : rid[3];
-            if (j > rmax) {
-                // every row of the pass counts at all four columns
+            } else if (j > row) {
+                // all four columns right of the row's diagonal
 #pragma unroll
-                for (int q = 0; q < (int)TC_ROWS; ++q) {
-                    if ((q > 0 || !first) && (u32)q < np) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const u32 kk = key_of(lane_of_dyn(v[q], c), DT);
-                            if (kk < bk[c]) {
-                                bk[c] = kk;
-                                bi[c] = rid[q];
-                            }
-                        }
+                for (int c = 0; c < 4; ++c) {
+                    const u32 kk = key_of(lane_of_dyn(v[t], c), DT);
+                    if (kk < bk[4 * t + c]) {
+                        bk[4 * t + c] = kk;
+                        bi[4 * t + c] = row;
                     }
                 }
-            } else {
+            } else if (j + 3u > row) {
+                // the group that holds the row's diagonal
 #pragma unroll
-                for (int q = 0; q < (int)TC_ROWS; ++q) {
-                    if ((q > 0 || !first) && (u32)q < np && j + 3u > rid[q]) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const u32 kk = key_of(lane_of_dyn(v[q], c), DT);
-                            if (j + (u32)c > rid[q] && kk < bk[c]) {
-                                bk[c] = kk;
-                                bi[c] = rid[q];
-                            }
-                        }
+                for (int c = 0; c < 4; ++c) {
+                    const u32 kk = key_of(lane_of_dyn(v[t], c), DT);
+                    if (j + (u32)c > row && kk < bk[4 * t + c]) {
+                        bk[4 * t + c] = kk;
+                        bi[4 * t + c] = row;
                     }
                 }
             }
-            if (flags & TF_LAST) {
-                // fold the chunk's column minima into the bins
-                const uint4 lab = reinterpret_cast<const uint4*>(st + TC_ROWS * TC_ROW_BYTES)[ctid];
+        }
+        if (flags & TF_LAST) {
+            // fold the chunk's column minima into the bins
+            const unsigned char* lb = st + TC_ROW_BYTES;
+#pragma unroll
+            for (u32 t = 0; t < TC_G; ++t) {
+                const u32 j = c0 + 4u * (ctid + TC_CONS * t);
+                if (j >= c1)
+                    continue;
+                const uint2 lab = *reinterpret_cast<const uint2*>(lb + (j - cl0) * 2u);
+                const u32 L[4] = {lab.x & 0xFFFFu, lab.x >> 16, lab.y & 0xFFFFu, lab.y >> 16};
+                // columns j + c >= cmin lie right of the item's smallest row
+                const u32 cmin = j > r0 ? 0u : r0 + 1u - j;
                 u64 e[4];
                 u32 rel[4];
                 bool okc[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const u32 L = lane_of_dyn(lab, c), col = j + (u32)c;
-                    rel[c] = L - b0;
-                    okc[c] = (L != A) && (rel[c] < nb) && (col > r0);
-                    e[c] = ((u64)bk[c] << 32) | ((u64)bi[c] << 16) | col;
+                    rel[c] = L[c] - b0;
+                    okc[c] = (L[c] != A) && (rel[c] < nb) && ((u32)c >= cmin);
+                    e[c] = ((u64)bk[4 * t + c] << 32) | ((bi[4 * t + c] << 16) | (j + (u32)c));
                 }
                 u64 cur[4];
 #pragma unroll
@@ -397,13 +403,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             u64 mn = EDGE_INF;
             u64* dst = a.cout + (size_t)A * cn + b0;
             for (u32 b = ctid; b < nb; b += TC_CONS) {
-                const u64 v = bins[b];
+                const u64 x = bins[b];
                 bins[b] = EDGE_INF;
                 if (single)
-                    dst[b] = v;
-                else if (v != EDGE_INF)
-                    atomicMin(dst + b, v);
-                mn = v < mn ? v : mn;
+                    dst[b] = x;
+                else if (x != EDGE_INF)
+                    atomicMin(dst + b, x);
+                mn = x < mn ? x : mn;
             }
             mn = warp_min_u64(mn);
             if (lane == 0)

@@ -70,6 +70,7 @@ struct Workspace {
     u32 *first_child = nullptr, *next_sib = nullptr;
     u32 *pos = nullptr, *order = nullptr, *nsize = nullptr, *gap = nullptr, *st = nullptr;
     u32* a4_start = nullptr;   // Algorithm 4 fill: tile prefix per edge
+    unsigned short* label16 = nullptr;   // level-0 labels as 16 bits (n + 8 entries)
     // contraction matrices when M cannot serve as scratch (M == W)
     void* cscratch = nullptr;
     size_t cscratch_bytes = 0;
@@ -90,8 +91,9 @@ cudaError_t run_insert(const void* M, int64_t n, int dt, const void* w, void* Mo
                        cudaStream_t s);
 cudaError_t run_fill_trivial(int64_t n, void* M, cudaStream_t s);   // n == 1
 // level-0 contraction over the upper triangle fed by bulk copies
-// (contract_tma.cu); runs when |C_1| <= run_max, needs n % 4 == 0 and W and
-// ca.label 16-byte aligned; ca.bin_cap <= contract_tma_bin_cap(smem_optin)
+// (contract_tma.cu); runs when |C_1| <= run_max, needs n % 4 == 0, W and
+// ca.label16 16-byte aligned (ca.label16: n + 8 entries, written by the
+// level-0 step) and ca.bin_cap <= contract_tma_bin_cap(smem_optin)
 struct ContractArgs;
 u32 contract_tma_bin_cap(int smem_optin);
 cudaError_t launch_contract0_tma(const ContractArgs& ca, int dt, int blocks, u32 run_max, u32* status,

@@ -21,6 +21,7 @@ struct StepArgs {
     u32* status;
     u32 bin_cap;
     u32 update_comp = 1;   // 0: the caller maps comp[] through label[] later
+    unsigned short* label16 = nullptr;   // 16-bit copy of label[] (level 0 only)
 };
 
 // One Boruvka round's component bookkeeping, written once for a team (the
@@ -99,6 +100,8 @@ __device__ void step_body(const Team& t, const StepArgs& a)
         u32 p = a.par[x];
         u32 A = a.rootid[p];
         a.label[x] = A;
+        if (a.label16)
+            a.label16[x] = (unsigned short)A;
         if (p != x)
             a.mst[mst_base + x - a.rootid[x]] = a.best_in[x];
         atomicAdd(&a.cnt[A], 1u);
@@ -168,6 +171,7 @@ struct ContractArgs {
     u32* comp = nullptr;   // vertex -> component, mapped through label[] here when
     u32 n = 0;             // this round's step left it (|C_r| <= comp_max_c)
     u32 comp_max_c = 0;
+    const unsigned short* label16 = nullptr;   // level-0 labels as 16 bits (bulk-copy form)
 };
 
 // Column work of one contraction item with NR rows of W (level 0).  rows[]

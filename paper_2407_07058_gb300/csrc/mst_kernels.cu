@@ -449,6 +449,9 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         sa.ctr = ws.ctr;
         sa.status = status;
         sa.bin_cap = ws.bin_cap;
+        // level 0 of the upper-triangle path also keeps 16-bit labels (every
+        // component of round 1 has two or more vertices: ids < 32768)
+        sa.label16 = (r == 0 && vec && ws.bin_cap_t > 0) ? ws.label16 : nullptr;
         err = cudaMemsetAsync(&ws.ctr->bar, 0, 2 * sizeof(u32), s);
         if (err != cudaSuccess)
             return err;
@@ -492,6 +495,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
             // the copy ring, else one CTA per SM with all bins
             ContractArgs cat = ca;
             cat.bin_cap = ws.bin_cap_t;
+            cat.label16 = ws.label16;
             if ((err = launch_contract0_tma(cat, dt, ws.contract_blocks, ws.bin_cap_t, status, s)) !=
                 cudaSuccess)
                 return err;
