@@ -448,7 +448,7 @@ def run_ours(args, rank, world, local):
     tri = 2.0 * n * (n - 1)
     cand = {
         "k_fill": (prof["fill"], 4.0 * n * n),
-        "k_contract(W)+k_colmin_p": (prof["contract_w"], tri + 16.0 * c1 * c1),
+        "k_contract_tma+k_colmin_p": (prof["contract_w"], tri + 16.0 * c1 * c1),
         "k_rowmin_sym": (prof["rowmin"], tri),
     }
     dom = max(cand, key=lambda k: cand[k][0])
