@@ -466,6 +466,8 @@ def run_ours(args, rank, world, local):
     min_bytes = 2.0 * n * (n - 1) + 4.0 * n * n
     solve_frac = design_bytes / (ms_step / 1e3) / 1e9 / peak
     min_frac = min_bytes / (ms_step / 1e3) / 1e9 / peak
+    # the solve's own input and output: all of W read once, all of M written
+    wm_frac = 8.0 * n * n / (ms_step / 1e3) / 1e9 / peak
 
     # ---- warm start: insert one vertex into the solved matrix (Section 6.1)
     insert = None
@@ -553,7 +555,7 @@ def run_ours(args, rank, world, local):
             "phases_ms_per_step": {k: prof[k] / args.steps for k in appd.PHASES},
             "c1": c1,
             "hbm_frac_solve_design_bytes": solve_frac,
-            "hbm_frac_solve_min_bytes": min_frac,
+            "hbm_frac_solve_min_bytes": min_frac, "hbm_frac_solve_w_plus_m": wm_frac,
             "insert": insert,
             "batched": batched,
             "serving": serving,

@@ -389,19 +389,21 @@ __device__ __forceinline__ void contract_cols_w_upper(const u32* __restrict__ Wp
     }
 }
 
-// Column work of one item pass of up to 4 rows of C_r (levels >= 1):
-// entries are packed edges already, so a column reduces by a plain minimum.
+// Column work of one item pass of up to 8 rows of C_r (levels >= 1):
+// entries are packed edges already, so a column reduces by a plain minimum;
+// eight rows' loads are in flight before any is used.
 __device__ __forceinline__ void contract_cols_c(const u64* __restrict__ Cp, u32 cr,
                                                 const u32* __restrict__ label,
                                                 const u32* __restrict__ srows, u32 np, u32 A, u32 b0,
                                                 u32 nb, u64* bins)
 {
-    constexpr int NR = 4;
+    constexpr int NR = 8;
     const u32 tid = threadIdx.x, bd = blockDim.x;
-    const u64* rp[NR];
+    u32 rr[NR];
 #pragma unroll
     for (int q = 0; q < NR; ++q)
-        rp[q] = Cp + (size_t)srows[(u32)q < np ? q : 0] * cr;
+        rr[q] = srows[(u32)q < np ? q : 0];
+    auto rowp = [&](int q) { return Cp + (size_t)rr[q] * cr; };
     auto update = [&](u32 L, u64 e) {
         u32 rel = L - b0;
         if (L != A && rel < nb) {
@@ -415,10 +417,10 @@ __device__ __forceinline__ void contract_cols_c(const u64* __restrict__ Cp, u32 
         const u32 n2 = cr >> 1;
         for (u32 g = tid; g < n2; g += bd) {
             uint4 v[NR];
-            v[0] = ld_stream_v4(rp[0] + 2 * g);
+            v[0] = ld_stream_v4(rowp(0) + 2 * g);
 #pragma unroll
             for (int q = 1; q < NR; ++q)
-                v[q] = ((u32)q < np) ? ld_stream_v4(rp[q] + 2 * g) : v[0];
+                v[q] = ((u32)q < np) ? ld_stream_v4(rowp(q) + 2 * g) : v[0];
             const uint2 lab = *reinterpret_cast<const uint2*>(label + 2 * g);
             u64 e0 = EDGE_INF, e1 = EDGE_INF;
 #pragma unroll
@@ -434,11 +436,11 @@ __device__ __forceinline__ void contract_cols_c(const u64* __restrict__ Cp, u32 
         jt = 2 * n2;
     }
     for (u32 j = jt + tid; j < cr; j += bd) {
-        u64 e = rp[0][j];
+        u64 e = rowp(0)[j];
 #pragma unroll
         for (int q = 1; q < NR; ++q) {
             if ((u32)q < np) {
-                u64 x = rp[q][j];
+                u64 x = rowp(q)[j];
                 e = x < e ? x : e;
             }
         }
@@ -480,9 +482,10 @@ __device__ __forceinline__ void contract_item(const ContractArgs& a, u32 item, u
         }
     }
     __syncthreads();
-    // rows in passes of at most 4 (register budget); bins merge passes
-    for (u32 p0 = 0; p0 < nrows; p0 += 4) {
-        const u32 np = min(4u, nrows - p0);
+    // rows in passes of at most 4 (W) or 8 (C_r, cheaper per entry) for the
+    // register budget; bins merge passes
+    for (u32 p0 = 0; p0 < nrows; p0 += (LEVEL0 ? 4u : 8u)) {
+        const u32 np = min(LEVEL0 ? 4u : 8u, nrows - p0);
         if (LEVEL0 && UPPER)
             contract_cols_w_upper<DT>((const u32*)a.cin, cr, a.label, s_rows + p0, np, A, b0, nb, bins);
         else if (LEVEL0)

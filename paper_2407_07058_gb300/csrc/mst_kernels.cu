@@ -452,21 +452,23 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         // level 0 of the upper-triangle path also keeps 16-bit labels (every
         // component of round 1 has two or more vertices: ids < 32768)
         sa.label16 = (r == 0 && vec && ws.bin_cap_t > 0) ? ws.label16 : nullptr;
-        err = cudaMemsetAsync(&ws.ctr->bar, 0, 2 * sizeof(u32), s);
-        if (err != cudaSuccess)
+        // every round at least halves the components, so round r has at most
+        // n >> r rows: rounds that cannot exceed the one-CTA limit skip the
+        // grid form (and its barrier reset)
+        const bool grid_step = (n >> r) > STEP_BLOCK_MAX_C;
+        if (grid_step && (err = cudaMemsetAsync(&ws.ctr->bar, 0, 2 * sizeof(u32), s)) != cudaSuccess)
             return err;
         void* args[] = {&sa};
         prof_begin(PH_STEP, s);
-        // no round can have more rows than n: small graphs skip the grid form
-        err = (n <= STEP_BLOCK_MAX_C) ? cudaSuccess
-                                      : cudaLaunchCooperativeKernel((const void*)k_step, dim3(ws.coop_blocks),
-                                                                    dim3(ws.coop_threads), args, 0, s);
+        err = grid_step ? cudaLaunchCooperativeKernel((const void*)k_step, dim3(ws.coop_blocks),
+                                                      dim3(ws.coop_threads), args, 0, s)
+                        : cudaSuccess;
         if (err == cudaSuccess) {
             k_step_block<<<1, STEP_BLOCK_THREADS, 0, s>>>(sa);
             err = cudaGetLastError();
         }
         prof_end(PH_STEP, s);
-        prof_launches(3);
+        prof_launches(grid_step ? 3 : 2);
         if (err != cudaSuccess)
             return err;
 
