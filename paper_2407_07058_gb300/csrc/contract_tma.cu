@@ -13,17 +13,19 @@
 //   * a producer warp claims items and, for every chunk of TC_CH columns and
 //     every row of the item that reaches the chunk (rows ascending), issues
 //     one bulk copy of that row's segment right of its diagonal into the
-//     next free ring stage (plus the chunk's 16-bit labels with the chunk's
-//     last row), completing on the stage's "full" mbarrier;
+//     next free ring stage, completing on the stage's "full" mbarrier;
 //   * TC_CONS consumer threads own TC_G interleaved 4-column groups of every
 //     chunk, keep the running minimum of their columns over the chunk's rows
-//     in registers and fold them into the bins once per chunk, then release
-//     the stage on its "empty" mbarrier.
+//     in registers and fold them into the bins once per chunk (the chunk's
+//     16-bit labels are read from L2, requested before the last row's work),
+//     then release the stage on its "empty" mbarrier.
 // One row per stage keeps the stages full (a component's rows are spread
 // over the matrix, so few of them reach the left part of a row range) and
-// gives each consumer 16 columns per stage to amortize the stage's fixed
-// work.  At the end of an item the consumers write the bins out and reset
-// them while the producer already streams the next item.
+// gives each consumer 12 columns per stage to amortize the stage's fixed
+// work.  The ring holds rows only, so the bins leave room for 24 consumer
+// warps (the consumers are latency-bound: more warps per SM, more speed).
+// At the end of an item the consumers write the bins out and reset them
+// while the producer already streams the next item.
 //
 // Every wait is bounded (BARRIER_TIMEOUT_NS): a wait that runs out sets the
 // CTA's abort flag, records DEV_TIMEOUT for the solve, every role leaves its
@@ -36,16 +38,14 @@ namespace appd {
 
 namespace {
 
-constexpr int TC_CONS_WARPS = 16;
+constexpr int TC_CONS_WARPS = 24;
 constexpr u32 TC_CONS = TC_CONS_WARPS * 32;     // consumer threads
 constexpr u32 TC_THREADS = TC_CONS + 32;        // plus one producer warp
-constexpr u32 TC_G = 4;                         // 4-column groups per consumer and chunk
+constexpr u32 TC_G = 3;                         // 4-column groups per consumer and chunk
 constexpr u32 TC_CH = 4 * TC_CONS * TC_G;       // columns per chunk
-constexpr u32 TC_STAGES = 3;
+constexpr u32 TC_STAGES = 4;
 constexpr u32 TC_ROW_BYTES = TC_CH * 4;
-// the chunk's labels, copied from a multiple of 8 columns (16-byte rule)
-constexpr u32 TC_LAB_BYTES = (TC_CH + 8) * 2;
-constexpr u32 TC_STAGE_BYTES = TC_ROW_BYTES + TC_LAB_BYTES;
+constexpr u32 TC_STAGE_BYTES = TC_ROW_BYTES;
 constexpr u32 TC_RING_BYTES = TC_STAGES * TC_STAGE_BYTES;
 static_assert(TC_STAGE_BYTES % 16 == 0, "stages start 16-byte aligned");
 
@@ -55,8 +55,7 @@ enum : u32 { TF_FIRST = 1, TF_LAST = 2, TF_END_ITEM = 4, TF_END = 8 };
 struct __align__(16) TcMeta {
     u32 c0, c1, row, flags;        // columns [c0, c1) of the chunk; the stage's row; TF_* bits
     u32 A, b0, nb, single;         // the item: group, bin range, one-chunk group
-    u32 r0, cl0, pad0, pad1;       // the item's smallest row; first column of the labels
-    u32 pad2[4];
+    u32 r0, pad0, pad1, pad2;      // the item's smallest row
 };
 
 __device__ __forceinline__ u32 smem_addr(const void* p) { return (u32)__cvta_generic_to_shared(p); }
@@ -120,6 +119,14 @@ __device__ __forceinline__ bool tc_wait(u64* bar, u32 parity, volatile u32* abor
             return false;
         }
     }
+}
+
+// 8-byte read-only load (four 16-bit labels)
+__device__ __forceinline__ uint2 ld_nc_u2(const void* p)
+{
+    uint2 v;
+    asm volatile("ld.global.nc.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
 }
 
 // first column group a row reaches: columns j with j + 3 > row, rounded to 4
@@ -229,9 +236,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                       (!more && c1 == cr ? TF_END_ITEM : 0u);
                     const u32 s0 = max(c0, dq);
                     const u32 rbytes = s0 < c1 ? (c1 - s0) * 4u : 0u;
-                    const bool lab = !more && c0 < c1;
-                    const u32 cl0 = c0 & ~7u, cl1 = (c1 + 7u) & ~7u;
-                    const u32 lbytes = lab ? (cl1 - cl0) * 2u : 0u;
                     u32 slot;
                     if (!(ok = take_slot(slot)))
                         break;
@@ -240,15 +244,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         uint4* mw = reinterpret_cast<uint4*>(&s_meta[slot]);
                         mw[0] = make_uint4(c0, c1, row, flags);
                         mw[1] = make_uint4(A, b0, nb, single);
-                        mw[2] = make_uint4(r0, cl0, 0u, 0u);
-                        if (rbytes + lbytes == 0) {
+                        mw[2] = make_uint4(r0, 0u, 0u, 0u);
+                        if (rbytes == 0) {
                             mbar_arrive(&s_full[slot]);
                         } else {
-                            mbar_arrive_tx(&s_full[slot], rbytes + lbytes);
-                            if (rbytes)
-                                bulk_load(st + (s0 - c0) * 4u, W + (size_t)row * cr + s0, rbytes, &s_full[slot]);
-                            if (lbytes)
-                                bulk_load(st + TC_ROW_BYTES, a.label16 + cl0, lbytes, &s_full[slot]);
+                            mbar_arrive_tx(&s_full[slot], rbytes);
+                            bulk_load(st + (s0 - c0) * 4u, W + (size_t)row * cr + s0, rbytes, &s_full[slot]);
                         }
                     }
                     __syncwarp();
@@ -316,9 +317,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             break;
         const uint4 w1 = mr[1], w2 = mr[2];
         const u32 c0 = w0.x, c1 = w0.y, row = w0.z;
-        const u32 A = w1.x, b0 = w1.y, nb = w1.z, single = w1.w, r0 = w2.x, cl0 = w2.y;
+        const u32 A = w1.x, b0 = w1.y, nb = w1.z, single = w1.w, r0 = w2.x;
         const unsigned char* st = ring + slot * TC_STAGE_BYTES;
         const uint4* rows = reinterpret_cast<const uint4*>(st);
+        // the chunk's labels at its last row, requested before the row work
+        // so that their latency overlaps it
+        uint2 labg[TC_G];
+#pragma unroll
+        for (u32 t = 0; t < TC_G; ++t) {
+            const u32 j = c0 + 4u * (ctid + TC_CONS * t);
+            labg[t] = ((flags & TF_LAST) && j < c1) ? ld_nc_u2(a.label16 + j) : make_uint2(0u, 0u);
+        }
         // all groups' 16 bytes at once; groups left of the row's segment
         // hold stale data and are not used
         uint4 v[TC_G];
@@ -362,13 +371,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         if (flags & TF_LAST) {
             // fold the chunk's column minima into the bins
-            const unsigned char* lb = st + TC_ROW_BYTES;
+
 #pragma unroll
             for (u32 t = 0; t < TC_G; ++t) {
                 const u32 j = c0 + 4u * (ctid + TC_CONS * t);
                 if (j >= c1)
                     continue;
-                const uint2 lab = *reinterpret_cast<const uint2*>(lb + (j - cl0) * 2u);
+                const uint2 lab = labg[t];
                 const u32 L[4] = {lab.x & 0xFFFFu, lab.x >> 16, lab.y & 0xFFFFu, lab.y >> 16};
                 // columns j + c >= cmin lie right of the item's smallest row
                 const u32 cmin = j > r0 ? 0u : r0 + 1u - j;

@@ -91,9 +91,9 @@ cudaError_t run_insert(const void* M, int64_t n, int dt, const void* w, void* Mo
                        cudaStream_t s);
 cudaError_t run_fill_trivial(int64_t n, void* M, cudaStream_t s);   // n == 1
 // level-0 contraction over the upper triangle fed by bulk copies
-// (contract_tma.cu); runs when |C_1| <= run_max, needs n % 4 == 0, W and
-// ca.label16 16-byte aligned (ca.label16: n + 8 entries, written by the
-// level-0 step) and ca.bin_cap <= contract_tma_bin_cap(smem_optin)
+// (contract_tma.cu); runs when |C_1| <= run_max, needs n % 4 == 0, W 16-byte
+// aligned, ca.label16 8-byte aligned (n + 8 entries, written by the level-0
+// step) and ca.bin_cap <= contract_tma_bin_cap(smem_optin)
 struct ContractArgs;
 u32 contract_tma_bin_cap(int smem_optin);
 cudaError_t launch_contract0_tma(const ContractArgs& ca, int dt, int blocks, u32 run_max, u32* status,
