@@ -608,13 +608,12 @@ appd_status appd_solve_host_async(const void* W_host, int64_t n, appd_dtype dt, 
         *off = (size_t)l * piece;
         return *off >= bytes ? 0 : (bytes - *off < piece ? bytes - *off : piece);
     };
-    // copy in once this buffer pair's previous copy out is done (which
-    // follows that pair's previous solve)
+    // copy in once this pair's previous solve, the only reader of dW[b], is
+    // done (the pair's previous copy out may still be running)
     for (int l = 0; l < PIPE_LANES; ++l) {
         size_t off;
         const size_t len = span(l, &off);
-        for (int m = 0; m < PIPE_LANES && e == cudaSuccess; ++m)
-            e = cudaStreamWaitEvent(p->in[l], p->ev_out[b][m], 0);
+        e = cudaStreamWaitEvent(p->in[l], p->ev_comp[b], 0);
         if (e == cudaSuccess && len)
             e = cudaMemcpyAsync((char*)p->dW[b] + off, (const char*)W_host + off, len, cudaMemcpyHostToDevice,
                                 p->in[l]);
