@@ -7,7 +7,9 @@ mixture (means N(0, 25 I), sigma 1), seeded; W (17.2 GB) is generated on the
 device and stays resident; each step writes the 17.2 GB matrix M.
 
 Metric: APPD entries per second (n^2 / seconds per solve), whole job.
-Prints one JSON line (rank 0).  See the design doc for the byte counts.
+Prints one JSON line (rank 0).  Roofline bytes per solve: the fill writes
+4 n^2; the round-1 minima read the upper triangle of W, 2 n (n - 1); the
+level-0 contraction reads it again and writes and re-reads P, 16 c1^2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload big|n16384|n16384u32|n1000]

@@ -15,7 +15,7 @@
  * holds the edge into tree1 and tree2, both sides are found by traversal, and
  * every pair (p in tree1, q in tree2) gets M(p,q) = M(q,p) = w(e).
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - Weights are compared by an order key: uint32 weights compare as
  *    unsigned integers; FP32 weights compare by IEEE-754 totalOrder
  *    (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN).  The output cell holds
