@@ -126,10 +126,12 @@ appd_status appd_solve_host(const void *W_host, int64_t n, appd_dtype dt, void *
  * appd_solve_host_async -- appd_solve_host without the wait, pipelined for a
  * stream of problems: enqueues the copy of W_host to the device, the solve
  * (on s) and the copy of M back to M_host, and returns.  Consecutive calls
- * overlap one call's copy back with the next call's copy in and solve (the
- * host link carries both directions at once).  The library keeps, per
- * device, two device buffer pairs (4 x 4 n^2 bytes, until
- * appd_release_workspaces) and two internal copy streams.  The solve is
+ * overlap one call's copy back with the next calls' copies in and solves
+ * (the host link carries both directions at once; a copy in waits only for
+ * the previous solve on its buffer pair).  The library keeps, per device,
+ * two device buffer pairs (4 x 4 n^2 bytes, until appd_release_workspaces)
+ * and eight internal copy streams (each direction's copy is split into four
+ * pieces, which moves more bytes per second over the link).  The solve is
  * ordered on s like appd_solve; the copy back is not: call
  * appd_solve_host_wait(s) and then synchronize s before reading M_host or
  * changing W_host.  Pinned host buffers (cudaHostAlloc) reach the link's
