@@ -158,8 +158,10 @@ appd_status appd_solve_host_wait(appd_stream_t s);
  * device and keeps the last call's contents (the kernel initialises what it
  * reads); calls whose kernels overlap on the GPU race on it, so order them.
  * The first call on a device looks up the array's address and sets a kernel
- * attribute; make it before any stream capture.  Device-side consistency
- * checks of this entry point are not reported by appd_last_device_status.
+ * attribute; make it before any stream capture.  Errors it detects on the
+ * device (an internal consistency check) are kept in a status word inside the
+ * array and reported, like every other entry point's, by
+ * appd_last_device_status; a failed solve leaves M unwritten.
  */
 appd_status appd_solve_noalloc(const void *W, int64_t n, appd_dtype dt, void *M, appd_stream_t s);
 
@@ -275,6 +277,17 @@ appd_status appd_probe_bounded_wait(int32_t limit_ms, appd_stream_t s);
 /* Frees every cached workspace on the current device (synchronizes it). */
 appd_status appd_release_workspaces(void);
 
+/*
+ * appd_debug_mark_failed -- failure injection on the host, for tests (no
+ * counterpart in the paper).  Sets the per-solve failure flag in every
+ * control block the library keeps on the current device (the single-solve
+ * workspace, every workspace slice of the batched path, the array of
+ * appd_solve_noalloc), as a solve whose bounded wait ran out would leave it.
+ * The next solve on each must start clean and give the exact result.
+ * Synchronizes the device.  Touches no GPU state besides those flags.
+ */
+appd_status appd_debug_mark_failed(void);
+
 /* ----------------------------------------------------------- profiling */
 /*
  * appd_profile_begin -- from now on the library records a CUDA event pair on
@@ -313,10 +326,26 @@ appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_s
 appd_status appd_server_submit(appd_server *sv, int64_t n, appd_dtype dt, appd_stream_t s,
                                uint64_t *req_id, void **W_slot);
 
+/* Admit up to count requests at once (ns[k] vertices, dtype dts[k]): the
+ * longest prefix of the list that fits the budget and the in-flight limit is
+ * admitted, *admitted receives its length, and req_ids[k] / W_slots[k] are
+ * filled for k < *admitted as appd_server_submit does; s waits (on the device)
+ * for all their allocations.  Returns APPD_ERR_BUSY when count > 0 and none
+ * fits, APPD_OK otherwise (including a partial admission). */
+appd_status appd_server_submit_many(appd_server *sv, int32_t count, const int64_t *ns,
+                                    const uint8_t *dts, appd_stream_t s, uint64_t *req_ids,
+                                    void **W_slots, int32_t *admitted);
+
 /* Queue an admitted request for solving: its W is complete once the work
  * enqueued on s before this call has run (the solve waits for that on the
  * device; the caller need not synchronize). */
 appd_status appd_server_commit(appd_server *sv, uint64_t req_id, appd_stream_t s);
+
+/* appd_server_commit for count requests at once (one device event for the
+ * group).  Either all are queued or, on an unknown or already committed id,
+ * none (APPD_ERR_NOT_FOUND / APPD_ERR_INVALID). */
+appd_status appd_server_commit_many(appd_server *sv, int32_t count, const uint64_t *req_ids,
+                                    appd_stream_t s);
 
 /* Collect finished requests: up to cap ids in done_ids and their device M
  * pointers in M_ptrs (valid until release); *n_done receives the count.
@@ -324,8 +353,18 @@ appd_status appd_server_commit(appd_server *sv, uint64_t req_id, appd_stream_t s
 appd_status appd_server_poll(appd_server *sv, uint64_t *done_ids, const void **M_ptrs,
                              int32_t cap, int32_t *n_done);
 
-/* Free a finished request's slot (its M pointer becomes invalid). */
-appd_status appd_server_release(appd_server *sv, uint64_t req_id);
+/* Free a request's slots (its M pointer becomes invalid): a finished
+ * request, or one admitted but never committed.  The memory is freed in
+ * stream order after the work enqueued on s so far, so the caller's reads of
+ * M (or writes of an uncommitted W) enqueued on s complete before a later
+ * request can reuse it; work on other streams must be ordered before s.
+ * APPD_ERR_BUSY for a committed request that has not finished. */
+appd_status appd_server_release(appd_server *sv, uint64_t req_id, appd_stream_t s);
+
+/* appd_server_release for count requests; all ids are checked first, so
+ * either all are released or none. */
+appd_status appd_server_release_many(appd_server *sv, int32_t count, const uint64_t *req_ids,
+                                     appd_stream_t s);
 
 /* Wait for in-flight work, free all slots and the server. */
 appd_status appd_server_destroy(appd_server *sv);

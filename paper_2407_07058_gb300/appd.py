@@ -29,10 +29,11 @@ EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host"
            "appd_solve_batched", "appd_batched_tuning", "appd_batched_autotune",
            "appd_batched_get_tuning", "appd_check_symmetric",
            "appd_last_device_status", "appd_probe_bounded_wait", "appd_release_workspaces",
-           "appd_profile_begin",
+           "appd_debug_mark_failed", "appd_profile_begin",
            "appd_profile_end", "appd_server_create",
-           "appd_server_submit", "appd_server_commit", "appd_server_poll", "appd_server_release",
-           "appd_server_destroy"]
+           "appd_server_submit", "appd_server_submit_many", "appd_server_commit",
+           "appd_server_commit_many", "appd_server_poll", "appd_server_release",
+           "appd_server_release_many", "appd_server_destroy"]
 
 _LOCK = threading.Lock()
 _LIB = None
@@ -77,9 +78,13 @@ def load(build_if_missing: bool = True):
             "appd_server_create": [ctypes.c_size_t, i32, ctypes.POINTER(vp)],
             "appd_server_submit": [vp, i64, ci, vp, ctypes.POINTER(u64), ctypes.POINTER(vp)],
             "appd_server_commit": [vp, u64, vp],
+            "appd_server_submit_many": [vp, i32, vp, vp, vp, vp, vp, ctypes.POINTER(i32)],
+            "appd_server_commit_many": [vp, i32, vp, vp],
             "appd_server_poll": [vp, vp, vp, i32, ctypes.POINTER(i32)],
-            "appd_server_release": [vp, u64],
+            "appd_server_release": [vp, u64, vp],
+            "appd_server_release_many": [vp, i32, vp, vp],
             "appd_server_destroy": [vp],
+            "appd_debug_mark_failed": [],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -291,6 +296,12 @@ def release_workspaces():
     _check(load().appd_release_workspaces(), "appd_release_workspaces")
 
 
+def debug_mark_failed():
+    """Set the failure flag of every control block the library keeps on the
+    current device, as a failed earlier solve would (test hook, see appd.h)."""
+    _check(load().appd_debug_mark_failed(), "appd_debug_mark_failed")
+
+
 class _DevPtr:
     def __init__(self, ptr: int, n: int, typestr: str):
         self.__cuda_array_interface__ = {"shape": (n, n), "typestr": typestr,
@@ -325,10 +336,31 @@ class Server:
         _check(code, "appd_server_submit")
         return rid.value, slot.value
 
+    def submit_many(self, ns, dts, stream=None):
+        """Admit the longest prefix of the requests (ns[k], dts[k]) that fits;
+        returns (ids, slot pointers) as numpy arrays of the admitted prefix."""
+        nn = np.ascontiguousarray(np.asarray(ns, dtype=np.int64))
+        dd = np.ascontiguousarray(np.asarray(dts, dtype=np.uint8))
+        cnt = len(nn)
+        ids = np.zeros(max(cnt, 1), dtype=np.uint64)
+        slots = np.zeros(max(cnt, 1), dtype=np.uint64)
+        k = ctypes.c_int32()
+        code = load().appd_server_submit_many(self._h, cnt, nn.ctypes.data, dd.ctypes.data,
+                                               _stream_ptr(stream), ids.ctypes.data,
+                                               slots.ctypes.data, ctypes.byref(k))
+        if code != 7:
+            _check(code, "appd_server_submit_many")
+        return ids[: k.value], slots[: k.value]
+
     def commit(self, rid: int, stream=None):
         """Queue the request; its W is complete after the work already on
         `stream` (default: the current stream)."""
         _check(load().appd_server_commit(self._h, rid, _stream_ptr(stream)), "appd_server_commit")
+
+    def commit_many(self, ids, stream=None):
+        ii = np.ascontiguousarray(np.asarray(ids, dtype=np.uint64))
+        _check(load().appd_server_commit_many(self._h, len(ii), ii.ctypes.data, _stream_ptr(stream)),
+               "appd_server_commit_many")
 
     def poll(self, cap: int = 1024):
         ids = (ctypes.c_uint64 * cap)()
@@ -337,8 +369,24 @@ class Server:
         _check(load().appd_server_poll(self._h, ids, ptrs, cap, ctypes.byref(k)), "appd_server_poll")
         return [(ids[i], ptrs[i]) for i in range(k.value)]
 
-    def release(self, rid: int):
-        _check(load().appd_server_release(self._h, rid), "appd_server_release")
+    def poll_arrays(self, cap: int = 4096):
+        """poll() as numpy arrays (ids, M pointers)."""
+        ids = np.zeros(cap, dtype=np.uint64)
+        ptrs = np.zeros(cap, dtype=np.uint64)
+        k = ctypes.c_int32()
+        _check(load().appd_server_poll(self._h, ids.ctypes.data, ptrs.ctypes.data, cap,
+                                       ctypes.byref(k)), "appd_server_poll")
+        return ids[: k.value], ptrs[: k.value]
+
+    def release(self, rid: int, stream=None):
+        """Free the request's slots after the work already on `stream` (its
+        reads of M) has run."""
+        _check(load().appd_server_release(self._h, rid, _stream_ptr(stream)), "appd_server_release")
+
+    def release_many(self, ids, stream=None):
+        ii = np.ascontiguousarray(np.asarray(ids, dtype=np.uint64))
+        _check(load().appd_server_release_many(self._h, len(ii), ii.ctypes.data,
+                                                _stream_ptr(stream)), "appd_server_release_many")
 
     def close(self):
         if self._h:

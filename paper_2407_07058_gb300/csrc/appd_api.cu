@@ -528,6 +528,11 @@ void pipe_destroy(HostPipe* p)
 {
     if (!p)
         return;
+    // the buffers are in use until the last solve on each pair (on a caller's
+    // stream) and the copies on the internal streams have finished
+    for (int i = 0; i < 2; ++i)
+        if (p->ev_comp[i])
+            cudaEventSynchronize(p->ev_comp[i]);
     for (int l = 0; l < PIPE_LANES; ++l)
         for (cudaStream_t st : {p->in[l], p->out[l]})
             if (st)
@@ -884,19 +889,47 @@ appd_status appd_last_device_status(appd_stream_t s)
             return st;
     }
     u32 h = 0;
-    e = cudaMemcpy(&h, status, 4, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess)
-        return cuda_fail(e);
-    if (h) {
-        e = cudaMemset(status, 0, 4);
+    // the library's status word, and the one that appd_solve_noalloc keeps
+    // in its static array (it allocates nothing, so it cannot share ours)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    u32* words[2] = {status, noalloc_status_word(dev)};
+    for (u32* wp : words) {
+        if (!wp)
+            continue;
+        u32 x = 0;
+        e = cudaMemcpy(&x, wp, 4, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess)
             return cuda_fail(e);
+        if (x) {
+            e = cudaMemset(wp, 0, 4);
+            if (e != cudaSuccess)
+                return cuda_fail(e);
+        }
+        h |= x;
     }
     if (h & DEV_TIMEOUT)
         return APPD_ERR_TIMEOUT;
     if (h & DEV_INTERNAL)
         return APPD_ERR_INTERNAL;
     return APPD_OK;
+}
+
+appd_status appd_debug_mark_failed(void)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return APPD_ERR_CUDA;
+    cudaError_t e = cudaDeviceSynchronize();
+    const u32 one = 1u;
+    if (e == cudaSuccess && g_ws[dev])
+        e = cudaMemcpy(&g_ws[dev]->ctr->bar.failed, &one, sizeof(u32), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = batch_runtime_mark_failed(g_brt[dev]);
+    if (e == cudaSuccess)
+        e = noalloc_mark_failed(dev);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
 }
 
 appd_status appd_release_workspaces(void)

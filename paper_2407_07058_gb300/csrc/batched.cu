@@ -58,6 +58,7 @@ struct BatchArgs {
     const u64* pst_off;   // graph g's pos at posst + pst_off[g], its table after n entries
     u64* best0;           // round-1 minima of all graphs (k_rowmin_batched)
     const u64* row_off;   // graph g's minima at best0 + row_off[g]
+    u32* gfail;           // per graph: 1 when its solve failed (the fill skips it)
 };
 
 constexpr int BATCH_THREADS = 512;
@@ -373,13 +374,16 @@ __device__ void contract_level_warps(const ContractArgs& a, u32 cr, u32 cn, u32 
 
 template <int DT>
 __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, u32* pos_g, u64* best0,
-                          const BatchArgs& b, unsigned char* smem, u32* s_rows, u64* s_red)
+                          u32* fail_g, const BatchArgs& b, unsigned char* smem, u32* s_rows,
+                          u64* s_red)
 {
     BlockTeam t;
     const u32 tid = threadIdx.x;
     if (n == 1) {
-        if (tid == 0)
+        if (tid == 0) {
             M[0] = 0u;
+            *fail_g = 0u;
+        }
         __syncthreads();
         return;
     }
@@ -393,6 +397,11 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, u32* po
         ctr->done = 0;
         ctr->mst_count = 0;
         ctr->jump_flag[0] = ctr->jump_flag[1] = ctr->jump_flag[2] = 0;
+        // the slice's control block outlives the graph: a failure recorded
+        // by an earlier graph (or a stale allocation) must not stop this one
+        ctr->bar.count = 0;
+        ctr->bar.abort = 0;
+        ctr->bar.failed = 0;
     }
     // round-1 minima come from k_rowmin_batched (best0)
     __syncthreads();
@@ -521,9 +530,12 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, u32* po
     la.status = b.status;
     leaf_body(t, la);
     __syncthreads();
-
     // the fill runs afterwards for every graph of the batch at once
-    // (k_fill_batched), reading pos and the sparse table from posst
+    // (k_fill_batched), reading pos and the sparse table from posst; a graph
+    // whose solve failed has no valid leaf order and is skipped there
+    if (tid == 0)
+        *fail_g = solve_failed(&ctr->bar) ? 1u : 0u;
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
@@ -549,11 +561,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
             continue;
         u32* pos_g = b.posst + b.pst_off[g];
         u64* best_g = b.best0 + b.row_off[g];
+        u32* fail_g = b.gfail + g;
         switch (b.dts[g]) {
-        case 1: solve_one<1>(w, W, M, n, pos_g, best_g, b, smem, s_rows, s_red); break;
-        case 2: solve_one<2>(w, W, M, n, pos_g, best_g, b, smem, s_rows, s_red); break;
-        case 3: solve_one<3>(w, W, M, n, pos_g, best_g, b, smem, s_rows, s_red); break;
-        default: solve_one<0>(w, W, M, n, pos_g, best_g, b, smem, s_rows, s_red); break;
+        case 1: solve_one<1>(w, W, M, n, pos_g, best_g, fail_g, b, smem, s_rows, s_red); break;
+        case 2: solve_one<2>(w, W, M, n, pos_g, best_g, fail_g, b, smem, s_rows, s_red); break;
+        case 3: solve_one<3>(w, W, M, n, pos_g, best_g, fail_g, b, smem, s_rows, s_red); break;
+        default: solve_one<0>(w, W, M, n, pos_g, best_g, fail_g, b, smem, s_rows, s_red); break;
         }
     }
 }
@@ -570,6 +583,8 @@ __global__ void __launch_bounds__(FILLB_THREADS) k_fill_batched(BatchArgs b, con
     extern __shared__ __align__(16) unsigned char smem[];
     const uint4 tl = tiles[blockIdx.x];   // graph, first column, first row, rows
     const u32 g = tl.x, n = b.ns[g];
+    if (*(volatile const u32*)(b.gfail + g))   // no valid leaf order: leave M unwritten
+        return;
     const u32* pos = b.posst + b.pst_off[g];
     switch (b.dts[g]) {
     case 1: fill_tile<1>(pos, pos + n, n, tl.y, tl.z, tl.w, b.fill_rows, b.mp[g], smem); break;
@@ -683,7 +698,8 @@ struct DescLayout {
     u32 ntiles, ntasks;
     size_t posst_words;   // leaf positions + sparse tables of every graph
     size_t rows;          // vertices of every graph (round-1 minima)
-    size_t arena_bytes;   // posst, then the minima (8-byte aligned)
+    size_t arena_bytes;   // posst, then the minima (8-byte aligned), then a failure flag per graph
+    size_t gfail_off;     // byte offset of the failure flags in the arena
 };
 
 // sparse-table levels of an n-vertex graph (as the leaf order builds it)
@@ -720,7 +736,8 @@ DescLayout desc_layout(const BatchDesc& d, u32 fill_rows)
     L.off[7] = a16(L.off[6] + 8 * cnt);
     L.off[8] = a16(L.off[7] + 16 * (size_t)L.ntiles);
     L.bytes = (L.off[8] + 8 * (size_t)L.ntasks + 255) & ~(size_t)255;
-    L.arena_bytes = ((L.posst_words * 4 + 7) & ~(size_t)7) + 8 * L.rows + 256;
+    L.gfail_off = ((L.posst_words * 4 + 7) & ~(size_t)7) + 8 * L.rows;
+    L.arena_bytes = L.gfail_off + 4 * cnt + 256;
     return L;
 }
 
@@ -780,6 +797,7 @@ BatchArgs make_args(const BatchRuntime& rt, void* dev, const DescLayout& L, u32 
     a.row_off = (const u64*)((char*)dev + L.off[6]);
     a.posst = (u32*)arena;
     a.best0 = (u64*)((char*)arena + ((L.posst_words * 4 + 7) & ~(size_t)7));
+    a.gfail = (u32*)((char*)arena + L.gfail_off);
     a.count = cnt;
     a.next = rt.d_next;
     a.slices = rt.d_slices;
@@ -864,6 +882,27 @@ void batch_runtime_destroy(BatchRuntime* rt)
 
 int64_t batch_runtime_cap(const BatchRuntime* rt) { return rt->cap; }
 
+cudaError_t batch_runtime_mark_failed(BatchRuntime* rt)
+{
+    if (!rt)
+        return cudaSuccess;
+    Workspace tmp;
+    const size_t per = (workspace_layout(tmp, nullptr, rt->cap) + 255) & ~(size_t)255;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < rt->nslices && e == cudaSuccess; ++i) {
+        Workspace w;
+        workspace_layout(w, (char*)rt->slice_mem + per * i, rt->cap);
+        const u32 one = 1u;
+        e = cudaMemcpy(&w.ctr->bar.failed, &one, sizeof(u32), cudaMemcpyHostToDevice);
+    }
+    return e;
+}
+
+cudaError_t preload_batched()
+{
+    return touch_kernels(k_batched, k_fill_batched, k_rowmin_batched);
+}
+
 // Enqueues the batch's kernels on s: round-1 minima of every graph, queue
 // reset, the per-graph MST and leaf order, the fill of every graph.
 static void enqueue_batch(const BatchRuntime& rt, const BatchArgs& a, const void* dev, const DescLayout& L,
@@ -898,21 +937,32 @@ cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cuda
         // one descriptor block and one arena per runtime: launches on the
         // runtime are ordered on its stream, so the next upload follows the
         // last kernel
+        // both grow to the next power of two (at least 4 MB): a growth
+        // frees the old buffer, which waits for the whole device, so it must
+        // stay rare when batches of changing size follow each other
+        auto grow = [](size_t need) {
+            size_t b = (size_t)4 << 20;
+            while (b < need)
+                b *= 2;
+            return b;
+        };
         if (rt.desc_bytes < L.bytes) {
             cudaFree(rt.d_desc);
             rt.d_desc = nullptr;
             rt.desc_bytes = 0;
-            if ((e = cudaMalloc(&rt.d_desc, L.bytes)) != cudaSuccess)
+            const size_t b = grow(L.bytes);
+            if ((e = cudaMalloc(&rt.d_desc, b)) != cudaSuccess)
                 return e;
-            rt.desc_bytes = L.bytes;
+            rt.desc_bytes = b;
         }
         if (rt.arena_bytes < L.arena_bytes) {
             cudaFree(rt.arena);
             rt.arena = nullptr;
             rt.arena_bytes = 0;
-            if ((e = cudaMalloc(&rt.arena, L.arena_bytes)) != cudaSuccess)
+            const size_t b = grow(L.arena_bytes);
+            if ((e = cudaMalloc(&rt.arena, b)) != cudaSuccess)
                 return e;
-            rt.arena_bytes = L.arena_bytes;
+            rt.arena_bytes = b;
         }
         fill_desc(d, fr, L, host);
         // pageable source: the copy is staged before the call returns

@@ -436,6 +436,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+cudaError_t preload_contract_tma()
+{
+    return touch_kernels(k_contract_tma<0>, k_contract_tma<1>, k_contract_tma<2>, k_contract_tma<3>);
+}
+
 u32 contract_tma_bin_cap(int smem_optin)
 {
     const long cap = ((long)smem_optin - (long)TC_RING_BYTES - 1024) / 8;

@@ -121,6 +121,12 @@ __global__ void k_diag_zero(u32* __restrict__ M, u32 n)
         M[(size_t)i * n + i] = 0u;
 }
 
+cudaError_t preload_fill()
+{
+    return touch_kernels(k_fill<0>, k_fill<1>, k_fill<2>, k_fill<3>, k_a4_count, k_a4_scan, k_diag_zero,
+                         k_a4_fill<0>, k_a4_fill<1>, k_a4_fill<2>, k_a4_fill<3>);
+}
+
 cudaError_t run_fill(Workspace& ws, int dt, void* M, cudaStream_t s)
 {
     const u32 n = (u32)ws.n;

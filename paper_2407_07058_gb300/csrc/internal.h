@@ -131,6 +131,10 @@ struct BatchDesc {
     std::vector<uint8_t> dt;
 };
 struct BatchRuntime;   // workspace slices + cached launch plans (batched.cu)
+// sets the failure flag of every workspace slice's control block (test hook)
+cudaError_t batch_runtime_mark_failed(BatchRuntime* rt);
+// the same for the no-allocation array on device dev (if set up there)
+cudaError_t noalloc_mark_failed(int dev);
 cudaError_t batch_runtime_create(int64_t cap, const BatchTuning& tune, BatchRuntime** out);
 void batch_runtime_destroy(BatchRuntime* rt);
 int64_t batch_runtime_cap(const BatchRuntime* rt);
@@ -145,8 +149,31 @@ int solve_on(Workspace& ws, u32* status, const void* W, int64_t n, int dt, void*
              cudaStream_t s, bool alg4);
 // the current device's status word
 u32* device_status_word();
+// the status word inside the no-allocation entry point's static array on
+// device dev (null before that entry point's first call there)
+u32* noalloc_status_word(int dev);
 cudaError_t workspace_create(int64_t cap, Workspace** out);
 void workspace_destroy(Workspace* w);
+
+// Loads kernels now (their attributes are queried), so that a later launch
+// does not pay the module's first load under lazy loading.
+template <class... K>
+cudaError_t touch_kernels(K... kern)
+{
+    cudaError_t e = cudaSuccess;
+    cudaFuncAttributes at;
+    ((e = (e == cudaSuccess) ? cudaFuncGetAttributes(&at, (const void*)kern) : e), ...);
+    return e;
+}
+// every kernel of a translation unit (mst_kernels.cu, contract_tma.cu,
+// leaf_order.cu, fill.cu, batched.cu)
+cudaError_t preload_mst();
+cudaError_t preload_contract_tma();
+cudaError_t preload_leaf();
+cudaError_t preload_fill();
+cudaError_t preload_batched();
+// all of the above
+cudaError_t preload_kernels();
 
 // sizes
 size_t contraction_scratch_bytes(int64_t n);

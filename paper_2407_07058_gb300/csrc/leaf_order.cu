@@ -42,6 +42,8 @@ __global__ void __launch_bounds__(512) k_leaf_order_block(LeafArgs a)
     leaf_body(t, a);
 }
 
+cudaError_t preload_leaf() { return touch_kernels(k_leaf_order, k_leaf_order_block); }
+
 cudaError_t run_leaf_order(Workspace& ws, u32* status, cudaStream_t s)
 {
     if (ws.n < 2)

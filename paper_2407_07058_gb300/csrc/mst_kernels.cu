@@ -358,6 +358,35 @@ cudaError_t set_smem(K kern, size_t bytes)
 
 }  // namespace
 
+cudaError_t preload_mst()
+{
+    return touch_kernels(k_rowmin<0>, k_rowmin<1>, k_rowmin<2>, k_rowmin<3>, k_rowmin_sym<0>, k_rowmin_sym<1>,
+                         k_rowmin_sym<2>, k_rowmin_sym<3>, k_step, k_step_block, k_mst_init, k_colmin_p, k_sym,
+                         k_contract<0, 1, true, true, true>, k_contract<1, 1, true, true, true>,
+                         k_contract<2, 1, true, true, true>, k_contract<3, 1, true, true, true>,
+                         k_contract<0, 1, true, true, false>, k_contract<1, 1, true, true, false>,
+                         k_contract<2, 1, true, true, false>, k_contract<3, 1, true, true, false>,
+                         k_contract<0, 1, false, false, true>, k_contract<1, 1, false, false, true>,
+                         k_contract<2, 1, false, false, true>, k_contract<3, 1, false, false, true>,
+                         k_contract<0, 1, false, false, false>, k_contract<1, 1, false, false, false>,
+                         k_contract<2, 1, false, false, false>, k_contract<3, 1, false, false, false>,
+                         k_contract<0, 0, false, false, true>);
+}
+
+cudaError_t preload_kernels()
+{
+    cudaError_t e = preload_mst();
+    if (e == cudaSuccess)
+        e = preload_contract_tma();
+    if (e == cudaSuccess)
+        e = preload_leaf();
+    if (e == cudaSuccess)
+        e = preload_fill();
+    if (e == cudaSuccess)
+        e = preload_batched();
+    return e;
+}
+
 size_t contraction_scratch_bytes(int64_t n)
 {
     size_t h = (size_t)(n / 2), q = (size_t)(n / 4);

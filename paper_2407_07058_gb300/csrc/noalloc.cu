@@ -54,7 +54,8 @@ struct NoallocWs {
     u64 *skey0, *skey1;
     u32 *hist, *first_child, *next_sib, *pos, *order, *nsize, *gap, *st;
     u64* cscratch;   // contraction matrices (used when M == W)
-    u32* status;     // internal-check flags of this entry point
+    u32* status;     // device-detected errors of this entry point (sticky until
+                     // appd_last_device_status reads and clears them)
 };
 
 // Round-1 row minima by one CTA (each warp a row); same result as the other
@@ -98,6 +99,11 @@ __device__ void noalloc_solve(const NoallocWs& w, const u32* W, u32* M, u32 n, u
         ctr->done = 0;
         ctr->mst_count = 0;
         ctr->jump_flag[0] = ctr->jump_flag[1] = ctr->jump_flag[2] = 0;
+        // the control block lives in the shared array: a failure recorded by
+        // an earlier call must not stop this one
+        ctr->bar.count = 0;
+        ctr->bar.abort = 0;
+        ctr->bar.failed = 0;
     }
     noalloc_rowmin<DT>(W, n, w.best0);
     __syncthreads();
@@ -198,6 +204,8 @@ __device__ void noalloc_solve(const NoallocWs& w, const u32* W, u32* M, u32 n, u
     la.status = w.status;
     leaf_body(t, la);
     __syncthreads();
+    if (solve_failed(&ctr->bar))   // no valid leaf order: leave M unwritten
+        return;
     for (u32 j0 = 0; j0 < n; j0 += FC)
         for (u32 r0 = 0; r0 < n; r0 += NOALLOC_FILL_ROWS)
             fill_tile<DT>(w.pos, w.st, n, j0, r0, min(NOALLOC_FILL_ROWS, n - r0), NOALLOC_FILL_ROWS, M,
@@ -299,6 +307,28 @@ cudaError_t noalloc_setup(int dev, NoallocDev& d)
 }
 
 }  // namespace
+
+cudaError_t noalloc_mark_failed(int dev)
+{
+    if (dev < 0 || dev >= 64)
+        return cudaSuccess;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na[dev].ready)
+        return cudaSuccess;
+    const u32 one = 1u;
+    return cudaMemcpy(&g_na[dev].ws.ctr->bar.failed, &one, sizeof(u32), cudaMemcpyHostToDevice);
+}
+
+// The status word of this device's no-allocation array, or null before the
+// first appd_solve_noalloc on the device (nothing has been recorded then).
+u32* noalloc_status_word(int dev)
+{
+    if (dev < 0 || dev >= 64)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    return g_na[dev].ready ? g_na[dev].ws.status : nullptr;
+}
+
 }  // namespace appd
 
 using namespace appd;

@@ -4,8 +4,11 @@
 // memory (its W and M slots).  It is admitted while the admitted total stays
 // within the budget (minus the server's fixed workspaces) and the in-flight
 // count below its limit; otherwise submit returns APPD_ERR_BUSY and the caller
-// retries after releasing finished requests.  Slots come from the
-// stream-ordered allocator.
+// retries after releasing finished requests.  Slots come from a stream-ordered
+// memory pool of the server's own whose release threshold is the budget, so
+// memory freed by one request is kept mapped for the next instead of being
+// returned to the driver at every synchronization (re-mapping hundreds of MB
+// costs milliseconds and shows up as latency spikes).
 //
 // Dispatch: a server thread owns NSLOT stream slots, each with its own
 // batched-kernel runtime (workspace slices) and single-solve workspace, so
@@ -69,7 +72,9 @@ struct appd_server {
     uint64_t next_id = 1;
     int device = 0;
     cudaStream_t alloc_stream = nullptr;
+    cudaMemPool_t pool = nullptr;                 // the slots' memory pool
     cudaEvent_t alloc_done = nullptr;             // the latest slot allocation
+    cudaEvent_t release_ready = nullptr;          // caller's stream at release
     std::vector<cudaEvent_t> event_pool;          // commit events, reused
     Slot slots[NSLOT];
     std::unordered_map<uint64_t, Req> reqs;
@@ -204,6 +209,23 @@ appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_s
     cudaError_t e = cudaStreamCreateWithFlags(&sv->alloc_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&sv->alloc_done, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&sv->release_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = sv->device;
+        e = cudaMemPoolCreate(&sv->pool, &props);
+    }
+    if (e == cudaSuccess) {
+        uint64_t keep = (uint64_t)budget_bytes;   // the attribute is a 64-bit unsigned value
+        e = cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    // load every kernel module now, so that no request pays a first load
+    if (e == cudaSuccess)
+        e = preload_kernels();
     for (Slot& sl : sv->slots) {
         if (e == cudaSuccess)
             e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
@@ -248,9 +270,9 @@ appd_status appd_server_submit(appd_server* sv, int64_t n, appd_dtype dt, appd_s
     r.dt = dt;
     r.bytes = bytes;
     std::lock_guard<std::mutex> lk(sv->mu);
-    cudaError_t e = cudaMallocAsync(&r.W, bytes, sv->alloc_stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&r.W, bytes, sv->pool, sv->alloc_stream);
     if (e == cudaSuccess)
-        e = cudaMallocAsync(&r.M, bytes, sv->alloc_stream);
+        e = cudaMallocFromPoolAsync(&r.M, bytes, sv->pool, sv->alloc_stream);
     // the caller fills W on s: s waits for the allocation (no host wait)
     if (e == cudaSuccess)
         e = cudaEventRecord(sv->alloc_done, sv->alloc_stream);
@@ -270,17 +292,81 @@ appd_status appd_server_submit(appd_server* sv, int64_t n, appd_dtype dt, appd_s
     return APPD_OK;
 }
 
+appd_status appd_server_submit_many(appd_server* sv, int32_t count, const int64_t* ns,
+                                    const uint8_t* dts, appd_stream_t s, uint64_t* req_ids,
+                                    void** W_slots, int32_t* admitted)
+{
+    if (!sv || count < 0 || !admitted || (count > 0 && (!ns || !dts || !req_ids || !W_slots)))
+        return APPD_ERR_INVALID;
+    *admitted = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        if (ns[k] <= 0 || !dtype_ok((int)dts[k]))
+            return APPD_ERR_INVALID;
+        if (ns[k] > 65536)
+            return APPD_ERR_TOO_LARGE;
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    cudaError_t e = cudaSuccess;
+    int32_t k = 0;
+    for (; k < count; ++k) {
+        const size_t bytes = (size_t)ns[k] * (size_t)ns[k] * 4;
+        if ((int32_t)sv->reqs.size() >= sv->max_inflight ||
+            sv->reserved + sv->used + 2 * bytes > sv->budget)
+            break;
+        Req r;
+        r.id = sv->next_id++;
+        r.n = ns[k];
+        r.dt = (appd_dtype)dts[k];
+        r.bytes = bytes;
+        e = cudaMallocFromPoolAsync(&r.W, bytes, sv->pool, sv->alloc_stream);
+        if (e == cudaSuccess)
+            e = cudaMallocFromPoolAsync(&r.M, bytes, sv->pool, sv->alloc_stream);
+        if (e != cudaSuccess) {
+            if (r.W)
+                cudaFreeAsync(r.W, sv->alloc_stream);
+            break;
+        }
+        sv->used += 2 * bytes;
+        req_ids[k] = r.id;
+        W_slots[k] = r.W;
+        sv->reqs.emplace(r.id, r);
+    }
+    *admitted = k;
+    if (k > 0) {
+        // s waits (on the device) for every allocation made so far
+        cudaError_t e2 = cudaEventRecord(sv->alloc_done, sv->alloc_stream);
+        if (e2 == cudaSuccess)
+            e2 = cudaStreamWaitEvent((cudaStream_t)s, sv->alloc_done, 0);
+        if (e2 != cudaSuccess)
+            return APPD_ERR_CUDA;
+    }
+    if (e != cudaSuccess && k == 0)
+        return e == cudaErrorMemoryAllocation ? APPD_ERR_NOMEM : APPD_ERR_CUDA;
+    return (k == 0 && count > 0) ? APPD_ERR_BUSY : APPD_OK;
+}
+
 appd_status appd_server_commit(appd_server* sv, uint64_t req_id, appd_stream_t s)
 {
-    if (!sv)
+    return appd_server_commit_many(sv, 1, &req_id, s);
+}
+
+appd_status appd_server_commit_many(appd_server* sv, int32_t count, const uint64_t* req_ids,
+                                    appd_stream_t s)
+{
+    if (!sv || count < 0 || (count > 0 && !req_ids))
         return APPD_ERR_INVALID;
+    if (count == 0)
+        return APPD_OK;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        auto it = sv->reqs.find(req_id);
-        if (it == sv->reqs.end())
-            return APPD_ERR_NOT_FOUND;
-        if (it->second.committed)
-            return APPD_ERR_INVALID;
+        for (int32_t k = 0; k < count; ++k) {
+            auto it = sv->reqs.find(req_ids[k]);
+            if (it == sv->reqs.end())
+                return APPD_ERR_NOT_FOUND;
+            if (it->second.committed)
+                return APPD_ERR_INVALID;
+        }
+        // one event for the group: the requests' W are complete together
         cudaEvent_t ev = nullptr;
         if (!sv->event_pool.empty()) {
             ev = sv->event_pool.back();
@@ -292,9 +378,12 @@ appd_status appd_server_commit(appd_server* sv, uint64_t req_id, appd_stream_t s
             sv->event_pool.push_back(ev);
             return APPD_ERR_CUDA;
         }
-        it->second.ready = ev;
-        it->second.committed = true;
-        sv->pending.push_back(req_id);
+        for (int32_t k = 0; k < count; ++k) {
+            Req& r = sv->reqs[req_ids[k]];
+            r.ready = (k == 0) ? ev : nullptr;   // the first request carries the event
+            r.committed = true;
+            sv->pending.push_back(req_ids[k]);
+        }
     }
     sv->cv.notify_one();
     return APPD_OK;
@@ -324,21 +413,46 @@ appd_status appd_server_poll(appd_server* sv, uint64_t* done_ids, const void** M
     return APPD_OK;
 }
 
-appd_status appd_server_release(appd_server* sv, uint64_t req_id)
+appd_status appd_server_release(appd_server* sv, uint64_t req_id, appd_stream_t s)
 {
-    if (!sv)
+    return appd_server_release_many(sv, 1, &req_id, s);
+}
+
+appd_status appd_server_release_many(appd_server* sv, int32_t count, const uint64_t* req_ids,
+                                     appd_stream_t s)
+{
+    if (!sv || count < 0 || (count > 0 && !req_ids))
         return APPD_ERR_INVALID;
+    if (count == 0)
+        return APPD_OK;
     std::lock_guard<std::mutex> lk(sv->mu);
-    auto it = sv->reqs.find(req_id);
-    if (it == sv->reqs.end())
-        return APPD_ERR_NOT_FOUND;
-    Req& r = it->second;
-    if (r.committed && !r.done)
-        return APPD_ERR_BUSY;
-    cudaFreeAsync(r.W, sv->alloc_stream);
-    cudaFreeAsync(r.M, sv->alloc_stream);
-    sv->used -= 2 * r.bytes;
-    sv->reqs.erase(it);
+    for (int32_t k = 0; k < count; ++k) {
+        auto it = sv->reqs.find(req_ids[k]);
+        if (it == sv->reqs.end())
+            return APPD_ERR_NOT_FOUND;
+        if (it->second.committed && !it->second.done)
+            return APPD_ERR_BUSY;
+    }
+    // the slots are freed in stream order after the work the caller enqueued
+    // on s so far (its reads of M, or its writes of an uncommitted W), so the
+    // pool cannot hand the memory to a later request while that work runs
+    cudaError_t e = cudaEventRecord(sv->release_ready, (cudaStream_t)s);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(sv->alloc_stream, sv->release_ready, 0);
+    if (e != cudaSuccess)
+        return APPD_ERR_CUDA;
+    for (int32_t k = 0; k < count; ++k) {
+        auto it = sv->reqs.find(req_ids[k]);
+        Req& r = it->second;
+        if (r.ready) {   // committed but never launched: its event returns to the pool
+            sv->event_pool.push_back(r.ready);
+            r.ready = nullptr;
+        }
+        cudaFreeAsync(r.W, sv->alloc_stream);
+        cudaFreeAsync(r.M, sv->alloc_stream);
+        sv->used -= 2 * r.bytes;
+        sv->reqs.erase(it);
+    }
     return APPD_OK;
 }
 
@@ -367,10 +481,14 @@ appd_status appd_server_destroy(appd_server* sv)
         cudaEventDestroy(ev);
     if (sv->alloc_done)
         cudaEventDestroy(sv->alloc_done);
+    if (sv->release_ready)
+        cudaEventDestroy(sv->release_ready);
     if (sv->alloc_stream) {
         cudaStreamSynchronize(sv->alloc_stream);
         cudaStreamDestroy(sv->alloc_stream);
     }
+    if (sv->pool)
+        cudaMemPoolDestroy(sv->pool);
     for (Slot& sl : sv->slots) {
         batch_runtime_destroy(sl.rt);
         workspace_destroy(sl.ws);

@@ -144,5 +144,8 @@ def test_server_argument_errors_need_no_gpu():
     assert lib.appd_server_create(1 << 30, 0, ctypes.byref(h)) == 1
     assert lib.appd_server_submit(None, 10, 0, None, None, None) == 1
     assert lib.appd_server_commit(None, 1, None) == 1
-    assert lib.appd_server_release(None, 1) == 1
+    assert lib.appd_server_release(None, 1, None) == 1
+    assert lib.appd_server_submit_many(None, 1, None, None, None, None, None, None) == 1
+    assert lib.appd_server_commit_many(None, 1, None, None) == 1
+    assert lib.appd_server_release_many(None, 1, None, None) == 1
     assert lib.appd_server_destroy(None) == 1

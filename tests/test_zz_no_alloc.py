@@ -5,12 +5,14 @@ runs inside a memory pool or arena owned by a framework -- and keeps all its
 scratch in a fixed 4 MiB device array inside the library, which limits it to
 n <= 1024.  The test calls it through the C ABI and compares it with
 appd_solve bit for bit (the results are exact), twice in a row, since the
-array is shared and keeps the previous call's contents.  This file is
-collected last on purpose."""
+array is shared and keeps the previous call's contents, and with the CPU
+oracle, for both orders (minimax and widest paths).  This file is collected
+last on purpose."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from paper_2407_07058_gb300 import appd
 
@@ -46,6 +48,24 @@ def test_noalloc_matches_solve_on_two_calls_in_a_row():
             torch.cuda.synchronize()
             assert appd.last_device_status() == 0
             assert torch.equal(out, ref), f"call {call}: n={n} differs from appd_solve"
+            got = out.cpu().numpy().view(np.uint32)
+            assert np.array_equal(got, oracle.appd(W).view(np.uint32)), f"n={n} differs from the oracle"
+
+
+@pytest.mark.gpu
+def test_noalloc_widest_matches_oracle():
+    lib = appd.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    for W in _cases():
+        n = W.shape[0]
+        dt = (appd.F32 if W.dtype == np.float32 else appd.U32) | appd.WIDEST
+        T = _dev(W)
+        out = torch.full_like(T, -1)
+        assert lib.appd_solve_noalloc(T.data_ptr(), n, dt, out.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        assert appd.last_device_status() == 0
+        got = out.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, oracle.appd(W, widest=True).view(np.uint32)), f"widest n={n}"
 
 
 @pytest.mark.gpu
