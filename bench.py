@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-insert", action="store_true")
+    p.add_argument("--no-configs", action="store_true")
     return p.parse_args()
 
 
@@ -101,7 +102,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -171,6 +172,78 @@ def ncu_traffic(kernel: str):
         return ent["bytes_per_launch_full"]
     except Exception:
         return None
+
+
+def device_matrix(kind: str, n: int, dev, stream):
+    """The workload's W generated on the device (same bytes as host_matrix)."""
+    import torch
+
+    import synth
+    if kind == "u32":
+        W = torch.empty((n, n), dtype=torch.int32, device=dev)
+        synth.device_hash_u32(3, n, W.data_ptr(), stream.cuda_stream)
+    else:
+        pts = torch.from_numpy(points_for(kind, n)).to(dev)
+        W = torch.empty((n, n), dtype=torch.float32, device=dev)
+        synth.device_euclid(pts.data_ptr(), n, pts.shape[1], W.data_ptr(), stream.cuda_stream)
+        del pts
+    return W
+
+
+def bench_configs(dev, peak: float, reps: int = 10):
+    """The smaller single-solve configurations (n = 1000 GMM, n = 16384
+    uniform FP32, n = 16384 uint32 ties): median device time of a solve over
+    reps launches, entries/s, and the solve's W-read-plus-M-write bytes over
+    that time as a fraction of the HBM peak.  At n = 16384 the Algorithm 4
+    form (appd_solve_alg4: the paper's per-edge cross-block fill) is timed
+    beside the tiled fill, phase by phase."""
+    import torch
+
+    from paper_2407_07058_gb300 import appd
+    st = torch.cuda.current_stream()
+    out = {}
+    for name in ("n1000", "n16384", "n16384u32"):
+        wl = WORKLOADS[name]
+        n = wl["n"]
+        W = device_matrix(wl["kind"], n, dev, st)
+        M = torch.empty_like(W)
+        for _ in range(3):
+            appd.solve(W, out=M)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            appd.solve(W, out=M)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        ent = {"workload": wl["desc"], "ms": ms, "entries_per_s": n * n / (ms / 1e3),
+               "hbm_frac_w_plus_m": 8.0 * n * n / (ms / 1e3) / 1e9 / peak,
+               "l2": "W and M fit in L2" if 8 * n * n < 120e6 else "W and M larger than L2"}
+        if name == "n16384":
+            ph = {}
+            for alg4 in (False, True):
+                for _ in range(2):
+                    appd.solve(W, out=M, alg4=alg4)
+                torch.cuda.synchronize()
+                appd.profile_begin()
+                for _ in range(reps):
+                    appd.solve(W, out=M, alg4=alg4)
+                prof = appd.profile_end()
+                ph["alg4" if alg4 else "tiled"] = {k: prof[k] / reps for k in appd.PHASES[:6]}
+            ent["fill_ms_tiled"] = ph["tiled"]["fill"]
+            ent["fill_ms_alg4_form"] = ph["alg4"]["fill"]
+            ent["solve_ms_alg4_form"] = sum(ph["alg4"].values())
+            ent["fill_gbs_tiled"] = 4.0 * n * n / (ph["tiled"]["fill"] / 1e3) / 1e9
+            ent["fill_gbs_alg4_form"] = 4.0 * n * n / (ph["alg4"]["fill"] / 1e3) / 1e9
+        if appd.last_device_status() != 0:
+            raise RuntimeError(f"device status error in {name}")
+        out[name] = ent
+        del W, M
+        torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(kind: str, n_full: int, budget_s: float = 12.0):
@@ -263,88 +336,192 @@ def serving_requests(count: int, seed: int = 5):
     return ns, dts
 
 
-def run_serving(sv, ns, dts, arrivals, dev, seed: int = 5):
-    """Drives the server: requests arrive at `arrivals` (s, relative); each is
-    admitted when the budget allows, its W generated into the slot on the
-    device (stream-ordered: the server's solve waits for it on the device),
-    then committed; completions are polled and released.  Returns per-request
-    latency (arrival -> completion seen), host time to enqueue the ingress,
-    and the wall time."""
-    import collections
+class ServingInputs:
+    """Inputs of the serving mix, staged on the device before any timing.
 
+    Request k has n = ns[k] vertices; an FP32 request carries a 2-D point set
+    (5-component mixture, means uniform in [0, 10]^2, sigma 0.5, seeded by
+    seed * 1000003 + k) whose distances are computed in FP32 arithmetic when
+    the request is generated; a uint32 request carries hashed weights in
+    [0, 2^16) with that seed.  Generation writes W into the request's slot
+    on the device (one launch per admission group)."""
+
+    def __init__(self, ns, dts, dev, seed: int = 5):
+        import torch
+
+        import synth
+        self.ns = np.asarray(ns, dtype=np.int64)
+        self.dts = np.asarray(dts, dtype=np.int64)
+        self.seeds = (seed * 1000003 + np.arange(len(ns))).astype(np.uint64)
+        self.pts_host = {}
+        off = np.zeros(len(ns), dtype=np.int64)
+        chunks, acc = [], 0
+        for k in np.nonzero(self.dts == 0)[0]:
+            p = synth.gmm_points(int(self.ns[k]), 2, 5, sigma=0.5, seed=int(self.seeds[k]),
+                                 mean_box=10.0)
+            self.pts_host[int(k)] = p
+            off[k] = acc
+            chunks.append(p.reshape(-1))
+            acc += p.size
+        flat = np.concatenate(chunks) if chunks else np.zeros(2, np.float32)
+        self.pts_dev = torch.from_numpy(flat).to(dev)
+        base = self.pts_dev.data_ptr()
+        self.pts_ptr = np.where(self.dts == 0, base + 4 * off, 0).astype(np.uint64)
+
+    def descs(self, idx, slots):
+        import synth
+        idx = np.asarray(idx, dtype=np.int64)
+        return synth.request_descs(slots, self.pts_ptr[idx], self.ns[idx], self.dts[idx],
+                                   self.seeds[idx], d=2)
+
+    def host_matrix(self, k: int) -> np.ndarray:
+        """Request k's W on the host, from the host twin of the generator."""
+        import synth
+        if self.dts[k]:
+            return synth.hash_u32(int(self.ns[k]), seed=int(self.seeds[k]))
+        return synth.euclid32(self.pts_host[int(k)])
+
+
+def _upload(desc, dev):
+    import torch
+    return torch.from_numpy(desc.view(np.uint8)).to(dev, non_blocking=True)
+
+
+def run_serving(sv, inp, idx, arrivals, dev, on_done=None):
+    """Drives the server with the requests idx (arrival times `arrivals`, s,
+    relative, ascending): arrived requests are admitted in order as the
+    budget allows (one submit call for every request that fits), their W
+    generated into the slots by one device launch, and the group committed
+    with one call (the solves wait for the generation on the device);
+    completions are polled and released in groups.  on_done(k, M_ptr), if
+    given, runs before request k is released.  Returns per-request latency
+    (arrival -> completion seen), host time to enqueue each group's ingress
+    per request, and the wall time."""
     import torch
 
     import synth
     from paper_2407_07058_gb300 import appd
-    N = len(ns)
+    idx = np.asarray(idx, dtype=np.int64)
+    N = len(idx)
     st = torch.cuda.current_stream()
     lat = np.zeros(N)
     ingress = []
-    waiting = collections.deque()
     owner = {}
-    i = done = 0
+    keep = []          # descriptor uploads in flight (stream-ordered reuse)
+    arrived = head = done = 0
     t0 = time.perf_counter()
     while done < N:
         now = time.perf_counter() - t0
-        while i < N and arrivals[i] <= now:
-            waiting.append(i)
-            i += 1
+        while arrived < N and arrivals[arrived] <= now:
+            arrived += 1
         progressed = False
-        while waiting:
-            k = waiting[0]
-            n, dt = int(ns[k]), int(dts[k])
-            r = sv.submit(n, appd.U32 if dt else appd.F32, st)
-            if r is None:
-                break
-            waiting.popleft()
-            rid, slot = r
-            tg = time.perf_counter()
-            if dt:
-                synth.device_hash_u32(seed * 1000003 + k, n, slot, st.cuda_stream)
-            else:
-                pts = torch.from_numpy(synth.gmm_points(n, 2, 5, sigma=0.5, seed=seed * 1000003 + k,
-                                                        mean_box=10.0)).to(dev, non_blocking=False)
-                synth.device_euclid(pts.data_ptr(), n, 2, slot, st.cuda_stream)
-            ingress.append(time.perf_counter() - tg)
-            sv.commit(rid, st)       # the solve waits for the generation on the device
-            owner[rid] = k
-            progressed = True
-        for rid, _ in sv.poll(4096):
-            k = owner.pop(rid)
-            lat[k] = time.perf_counter() - t0 - arrivals[k]
-            sv.release(rid)
-            done += 1
+        if head < arrived:
+            sel = idx[head:arrived]
+            ids, slots = sv.submit_many(inp.ns[sel], inp.dts[sel], st)
+            k = len(ids)
+            if k:
+                tg = time.perf_counter()
+                desc, tiles = inp.descs(sel[:k], slots)
+                d_dev = _upload(desc, dev)
+                synth.device_requests(d_dev.data_ptr(), k, tiles, st.cuda_stream)
+                keep.append(d_dev)
+                sv.commit_many(ids, st)
+                ingress.append((time.perf_counter() - tg) / k)
+                owner.update(zip(ids.tolist(), range(head, head + k)))
+                head += k
+                progressed = True
+                if len(keep) > 64:
+                    keep = keep[-8:]
+        ids, ptrs = sv.poll_arrays(4096)
+        if len(ids):
+            tdone = time.perf_counter() - t0
+            for rid, ptr in zip(ids.tolist(), ptrs.tolist()):
+                j = owner.pop(rid)
+                lat[j] = tdone - arrivals[j]
+                if on_done is not None:
+                    on_done(int(idx[j]), ptr)
+            sv.release_many(ids, st)
+            done += len(ids)
             progressed = True
         if not progressed:
-            time.sleep(0.0001)
+            time.sleep(0.00005)
+    torch.cuda.synchronize()
     return lat, np.array(ingress), time.perf_counter() - t0
 
 
+def one_by_one(inp, idx, dev):
+    """The same requests one at a time: generate W, then one plain appd_solve,
+    on one stream.  Returns (wall seconds, device seconds)."""
+    import torch
+
+    import synth
+    from paper_2407_07058_gb300 import appd
+    idx = np.asarray(idx, dtype=np.int64)
+    nmax = int(inp.ns[idx].max())
+    Wb = torch.empty(nmax * nmax, dtype=torch.float32, device=dev)
+    Mb = torch.empty_like(Wb)
+    desc, _ = inp.descs(idx, np.full(len(idx), Wb.data_ptr(), dtype=np.uint64))
+    tiles = (inp.ns[idx] ** 2 + synth.REQ_TILE - 1) // synth.REQ_TILE
+    desc["tile0"] = 0
+    d_dev = _upload(desc, dev)
+    st = torch.cuda.current_stream()
+
+    def run(ks):
+        for q in ks:
+            n = int(inp.ns[idx[q]])
+            synth.device_requests(d_dev.data_ptr() + desc.itemsize * q, 1, int(tiles[q]), st.cuda_stream)
+            w = Wb[: n * n].view(n, n)
+            m = Mb[: n * n].view(n, n)
+            if inp.dts[idx[q]]:
+                w, m = w.view(torch.int32), m.view(torch.int32)
+            appd.solve(w, out=m)
+
+    run(range(min(64, len(idx))))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(st)
+    run(range(len(idx)))
+    e1.record(st)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, e0.elapsed_time(e1) / 1e3
+
+
 def bench_serving(dev, count: int = 20000):
-    """Continuous batching under a 40 GB budget: capacity at saturation, then
-    Poisson arrivals at 0.5x and 0.8x of it; graphs/s and p50/p99 latency."""
+    """Continuous batching under a 40 GB budget: capacity at saturation, the
+    same requests one at a time, then Poisson arrivals at 0.5x and 0.8x of
+    the capacity; graphs/s and p50/p99 latency."""
     from paper_2407_07058_gb300 import appd
     budget = 40 << 30
     ns, dts = serving_requests(count)
+    inp = ServingInputs(ns, dts, dev)
     sv = appd.Server(budget, 8192)
     try:
         # warm-up, then capacity: a saturating burst (all arrive at t = 0)
-        run_serving(sv, ns[:200], dts[:200], np.zeros(200), dev)
+        run_serving(sv, inp, np.arange(300), np.zeros(300), dev)
         m = min(count, 4000)
-        _, _, wall = run_serving(sv, ns[:m], dts[:m], np.zeros(m), dev)
+        _, _, wall = run_serving(sv, inp, np.arange(m), np.zeros(m), dev)
         cap = m / wall
+        wall1, dev1 = one_by_one(inp, np.arange(m), dev)
         out = {"workload": f"{count} requests, n log-uniform in [64, 8192], half FP32 2-D "
-                           "mixture distances, half uint32 uniform [0, 2^16); 40 GB budget",
-               "capacity_graphs_per_s": cap, "rates": []}
+                           "mixture distances (FP32 arithmetic), half uint32 uniform [0, 2^16); "
+                           "40 GB budget",
+               "capacity_graphs_per_s": cap,
+               "capacity_requests": m,
+               "one_by_one_graphs_per_s": m / wall1,
+               "one_by_one_device_graphs_per_s": m / dev1,
+               "served_vs_one_by_one": cap / (m / wall1),
+               "rates": []}
         rng = np.random.default_rng(55)
         for frac in (0.5, 0.8):
             lam = frac * cap
             arr = np.cumsum(rng.exponential(1.0 / lam, size=count))
-            lat, ing, wall = run_serving(sv, ns, dts, arr, dev)
+            lat, ing, wall = run_serving(sv, inp, np.arange(count), arr, dev)
             out["rates"].append({"rate_frac_of_capacity": frac, "rate_per_s": lam,
                                  "graphs_per_s": count / wall,
                                  "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                                  "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                                 "max_ms": 1e3 * float(lat.max()),
                                  "ingress_host_p50_ms": 1e3 * float(np.percentile(ing, 50))})
     finally:
         sv.close()
@@ -374,7 +551,9 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": "APPD entries/s", "value": value, "unit": "entries/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": "u32 order keys" + (" (FP32 input)" if wl["kind"] != "u32" else ""),
+        "data": "synthetic",
         "config": {"workload": wl["desc"], "n": wl["n"], "sample_n": n},
         "cpu_baseline": {"value": value, "unit": "entries/s", "cores": 1, "kind": "oracle",
                          "sample": f"each step: the oracle on an n={n} graph from the same "
@@ -404,14 +583,7 @@ def run_ours(args, rank, world, local):
     n, kind = wl["n"], wl["kind"]
     stream = torch.cuda.current_stream()
     # ---- inputs resident on the device
-    if kind == "u32":
-        W = torch.empty((n, n), dtype=torch.int32, device=dev)
-        synth.device_hash_u32(3, n, W.data_ptr(), stream.cuda_stream)
-    else:
-        pts = torch.from_numpy(points_for(kind, n)).to(dev)
-        W = torch.empty((n, n), dtype=torch.float32, device=dev)
-        synth.device_euclid(pts.data_ptr(), n, pts.shape[1], W.data_ptr(), stream.cuda_stream)
-        del pts
+    W = device_matrix(kind, n, dev, stream)
     M = torch.empty_like(W)
     torch.cuda.synchronize()
 
@@ -531,9 +703,14 @@ def run_ours(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(kind, n)
+    configs = None
+    if not args.no_configs:
+        del W, M
+        torch.cuda.empty_cache()
+        configs = bench_configs(dev, peak)
     batched = None
     if not args.no_batched:
-        del W, M
+        W = M = None
         torch.cuda.empty_cache()
         batched = bench_batched(max(3, min(args.steps, 10)), args.warmup, dev, rank, world)
     serving = None
@@ -545,7 +722,8 @@ def run_ours(args, rank, world, local):
         line = {
             "metric": "APPD entries/s", "value": value, "unit": "entries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32 order keys" + (" (FP32 input)" if kind != "u32" else ""),
             "data": "synthetic",
             "config": {"workload": wl["desc"], "n": n, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (W and M 4n^2 bytes each)"},
@@ -559,6 +737,7 @@ def run_ours(args, rank, world, local):
             "hbm_frac_solve_design_bytes": solve_frac,
             "hbm_frac_solve_min_bytes": min_frac, "hbm_frac_solve_w_plus_m": wm_frac,
             "insert": insert,
+            "configs": configs,
             "batched": batched,
             "serving": serving,
         }

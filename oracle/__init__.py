@@ -13,6 +13,8 @@ return the matrix of original weight bits in the same dtype (diagonal 0):
 - ``brute(W)``: all simple paths, Eq. 1-2, n <= 9.
 - ``prim(W)``: Prim order and the MST edge codes.
 - ``tree_rows(W, mst, sources)``: rows of M by traversing the MST.
+- ``prim_rows(W, order, mst, sources)``: rows of M from Prim's visiting order.
+- ``points_w(X)``: FP32 edge weights of a point set (fixed-order FMA distance).
 - ``insert(M, w)``: warm start, the matrix of G + p from G's (Section 6.1).
 
 Every function takes ``widest=True`` for the widest-path matrix (Section 4.2:
@@ -46,7 +48,7 @@ def build() -> str:
     if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-shared", "-fPIC",
-                               "-o", tmp, src])
+                               "-o", tmp, src, "-lm"])
         os.replace(tmp, out)
     return out
 
@@ -64,6 +66,8 @@ def _lib():
             lib.appd_oracle_prim.argtypes = [vp, i64, ci, vp, vp]
             lib.appd_oracle_tree_rows.argtypes = [vp, i64, ci, vp, vp, i64, vp]
             lib.appd_oracle_insert.argtypes = [vp, i64, ci, vp, vp]
+            lib.appd_oracle_prim_rows.argtypes = [vp, i64, ci, vp, vp, vp, i64, vp]
+            lib.appd_oracle_points_w.argtypes = [vp, i64, ci, vp]
             lib.appd_oracle_set_mutation.argtypes = [ci]
             lib.appd_oracle_order_key.argtypes = [ctypes.c_uint32, ci]
             lib.appd_oracle_order_key.restype = ctypes.c_uint32
@@ -142,6 +146,35 @@ def tree_rows(W: np.ndarray, mst: np.ndarray, sources, widest: bool = False) -> 
     _check(_lib().appd_oracle_tree_rows(Wc.ctypes.data, n, dt, mst.ctypes.data, src.ctypes.data,
                                         len(src), rows.ctypes.data), "appd_oracle_tree_rows")
     return rows
+
+
+def prim_rows(W: np.ndarray, order: np.ndarray, mst: np.ndarray, sources,
+              widest: bool = False) -> np.ndarray:
+    """Rows of M for the given sources, read off Prim's visiting order
+    (``order, mst = prim(W)``): M(order[a], order[b]) is the largest of the
+    edges that added order[a+1..b].  O(n) per row."""
+    Wc, n, dt = _prep(W, widest)
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.uint32))
+    order = np.ascontiguousarray(order, dtype=np.uint32)
+    mst = np.ascontiguousarray(mst, dtype=np.uint64)
+    rows = np.empty((len(src), n), dtype=Wc.dtype)
+    _check(_lib().appd_oracle_prim_rows(Wc.ctypes.data, n, dt, mst.ctypes.data, order.ctypes.data,
+                                        src.ctypes.data, len(src), rows.ctypes.data),
+           "appd_oracle_prim_rows")
+    return rows
+
+
+def points_w(X: np.ndarray) -> np.ndarray:
+    """FP32 edge weights of the complete graph of a point set: for i != j,
+    W(i,j) = sqrt(s) with s accumulated over the coordinates in order as
+    s = fma(t, t, s), t = X(i,k) - X(j,k), every step an FP32 rounding."""
+    Xc = np.ascontiguousarray(X, dtype=np.float32)
+    if Xc.ndim != 2:
+        raise ValueError("X must be n x d")
+    n, d = Xc.shape
+    W = np.empty((n, n), dtype=np.float32)
+    _check(_lib().appd_oracle_points_w(Xc.ctypes.data, n, d, W.ctypes.data), "appd_oracle_points_w")
+    return W
 
 
 def insert(M: np.ndarray, w: np.ndarray, widest: bool = False) -> np.ndarray:

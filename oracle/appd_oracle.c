@@ -49,11 +49,14 @@
  * Test-only routines in this file: the ascending (small-to-large) form of
  * Section 3, the (min,max) Floyd-Warshall variant named in Section 1 and
  * Table 1, brute-force enumeration of simple paths (Eq. 1-2 written out),
- * and per-source tree traversal for sampled rows at large n.
+ * per-source tree traversal for sampled rows at large n, rows read off
+ * Prim's visiting order (every row of a large matrix in O(n^2) total), and
+ * the FP32 edge weights of a point set (the complete graph of a dataset).
  *
  * A test can plant a mistake in this oracle (appd_oracle_set_mutation) to
  * check that the pins catch it; mutation 0 is the correct oracle.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -543,6 +546,100 @@ int appd_oracle_tree_rows(const uint32_t *W, int64_t n, int dtype, const uint64_
     free(best);
     free(seen);
     free_adj(&t);
+    return 0;
+}
+
+/* ------------------------------------------------ rows from Prim's order */
+/*
+ * Rows of M from Prim's visiting order (the MST step of Section 3), for
+ * checking every row of a large matrix in O(n) per row.  order[0..n-1] is the
+ * order in which appd_oracle_prim adds the vertices and mst[k-1] the edge that
+ * added order[k]; write delta_k for that edge's code.  For a < b:
+ *     M(order[a], order[b]) = the weight of the largest of delta_{a+1..b}.
+ * Lower bound: for each k in (a, b], order[a] lies in the first k vertices
+ * and order[b] does not, so every path between them crosses that cut, and
+ * Prim took delta_k as the smallest edge across it.  Upper bound, by
+ * induction on b: order[b] joined through an edge to some order[p], p < b,
+ * of weight delta_b; if p >= a, the path order[a] .. order[p] - order[b]
+ * stays within max(delta_{a+1..p}, delta_b); if p < a, that same edge
+ * crossed the cut at every step k in (p, b], so delta_k <= delta_b there and
+ * order[a] .. order[p] - order[b] stays within delta_b.
+ * rows (nsrc x n): row t is M(src[t], .), all-zero bits on the diagonal.
+ * Mutation 5 leaves out the edge that added the farther vertex (an
+ * off-by-one in the range), which a pin must catch.
+ */
+int appd_oracle_prim_rows(const uint32_t *W, int64_t n, int dtype, const uint64_t *mst,
+                          const uint32_t *order, const uint32_t *src, int64_t nsrc, uint32_t *rows)
+{
+    (void)dtype;
+    if (n <= 0 || n > 65536)
+        return -1;
+    int64_t *rank = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!rank)
+        return -2;
+    for (int64_t k = 0; k < n; ++k)
+        rank[order[k]] = k;
+    for (int64_t t = 0; t < nsrc; ++t) {
+        const int64_t a = rank[src[t]];
+        uint32_t *row = rows + t * n;
+        row[src[t]] = 0;
+        /* later vertices: running maximum of delta_{a+1..b} */
+        uint64_t best = 0;
+        for (int64_t b = a + 1; b < n; ++b) {
+            const uint64_t d = mst[b - 1];
+            if (g_mutation == 5) {
+                if (b > a + 1 && mst[b - 2] > best)
+                    best = mst[b - 2];
+                row[order[b]] = edge_bits(W, n, b > a + 1 ? best : d);
+                continue;
+            }
+            if (b == a + 1 || d > best)
+                best = d;
+            row[order[b]] = edge_bits(W, n, best);
+        }
+        /* earlier vertices: running maximum of delta_{b+1..a} */
+        best = 0;
+        for (int64_t b = a - 1; b >= 0; --b) {
+            const uint64_t d = mst[b];
+            if (b == a - 1 || d > best)
+                best = d;
+            row[order[b]] = edge_bits(W, n, best);
+        }
+    }
+    free(rank);
+    return 0;
+}
+
+/* ----------------------------------- weights of a point set (Sections 1, 4) */
+/*
+ * The complete graph of a point set (Section 1 turns a dataset into a
+ * complete graph; the experiments of Section 4 run on point datasets), with
+ * the Euclidean distance evaluated in FP32 in one fixed order:
+ *     s = 0;  for k = 0 .. d-1:  t = X(i,k) - X(j,k)  (rounded to FP32),
+ *                                s = fma(t, t, s)      (one rounding);
+ *     W(i,j) = sqrt(s)  (correctly rounded),   W(i,i) = +0.
+ * t for (j,i) is exactly -t for (i,j), so W is symmetric bit for bit.
+ * X is n x d row-major FP32; W receives n x n FP32 bit patterns.
+ */
+int appd_oracle_points_w(const float *X, int64_t n, int d, uint32_t *W)
+{
+    if (n < 0 || d < 1)
+        return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            float s = 0.0f;
+            if (i != j) {
+                for (int k = 0; k < d; ++k) {
+                    const float t = X[i * d + k] - X[j * d + k];
+                    s = fmaf(t, t, s);
+                }
+                s = sqrtf(s);
+            }
+            uint32_t b;
+            memcpy(&b, &s, sizeof b);
+            W[i * n + j] = b;
+        }
+    }
     return 0;
 }
 

@@ -74,6 +74,8 @@ def _lib():
                                                 ctypes.c_int]
             lib.synth_euclid_row.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                              ctypes.c_int64, ctypes.c_void_p]
+            lib.synth_euclid32_f32.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                               ctypes.c_void_p, ctypes.c_int]
             _LIB = lib
     return _LIB
 
@@ -112,6 +114,18 @@ def euclid(points: np.ndarray) -> np.ndarray:
     W = np.empty((n, n), dtype=np.float32)
     if _lib().synth_euclid_f32(pts.ctypes.data, n, d, W.ctypes.data, _threads()) != 0:
         raise RuntimeError("synth_euclid_f32 failed")
+    return W
+
+
+def euclid32(points: np.ndarray) -> np.ndarray:
+    """FP32 Euclidean matrix computed in FP32 arithmetic: s = fma(t, t, s) over
+    the coordinates in order with t = x_lo,k - x_hi,k, then a correctly rounded
+    sqrt (the serving mix's point requests; definition in synth.c)."""
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    n, d = pts.shape
+    W = np.empty((n, n), dtype=np.float32)
+    if _lib().synth_euclid32_f32(pts.ctypes.data, n, d, W.ctypes.data, _threads()) != 0:
+        raise RuntimeError("synth_euclid32_f32 failed")
     return W
 
 
@@ -160,6 +174,12 @@ def _cuda_lib():
             lib.synth_cuda_uniform01_f32.argtypes = [ctypes.c_uint64, ctypes.c_int64,
                                                      ctypes.c_void_p, ctypes.c_void_p]
             lib.synth_cuda_uniform01_f32.restype = ctypes.c_int
+            lib.synth_cuda_euclid32_f32.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                                    ctypes.c_void_p, ctypes.c_void_p]
+            lib.synth_cuda_euclid32_f32.restype = ctypes.c_int
+            lib.synth_cuda_requests.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                                ctypes.c_void_p]
+            lib.synth_cuda_requests.restype = ctypes.c_int
             _CUDA_LIB = lib
     return _CUDA_LIB
 
@@ -175,6 +195,44 @@ def device_hash_u32(seed: int, n: int, W_dev_ptr: int, stream: int = 0) -> None:
     rc = _cuda_lib().synth_cuda_hash_u32(seed, n, W_dev_ptr, stream)
     if rc != 0:
         raise RuntimeError(f"synth_cuda_hash_u32 failed: {rc}")
+
+
+def device_euclid32(points_dev_ptr: int, n: int, d: int, W_dev_ptr: int, stream: int = 0) -> None:
+    """Device twin of euclid32 (FP32-arithmetic distances)."""
+    rc = _cuda_lib().synth_cuda_euclid32_f32(points_dev_ptr, n, d, W_dev_ptr, stream)
+    if rc != 0:
+        raise RuntimeError(f"synth_cuda_euclid32_f32 failed: {rc}")
+
+
+REQ_DESC = np.dtype([("slot", "<u8"), ("pts", "<u8"), ("tile0", "<u8"), ("seed", "<u8"),
+                     ("n", "<u4"), ("kind", "<u4"), ("d", "<u4"), ("pad", "<u4")])
+REQ_TILE = 1024
+
+
+def request_descs(slots, pts_ptrs, ns, kinds, seeds, d: int = 2):
+    """Descriptors of serving requests for device_requests: kind 0 = FP32
+    points (euclid32 of the n x d points at pts_ptrs[k]), 1 = hashed uint32
+    weights with seeds[k].  Returns (descriptor array, total tiles)."""
+    cnt = len(ns)
+    desc = np.zeros(cnt, dtype=REQ_DESC)
+    nn = np.asarray(ns, dtype=np.int64)
+    tiles = (nn * nn + REQ_TILE - 1) // REQ_TILE
+    desc["slot"] = np.asarray(slots, dtype=np.uint64)
+    desc["pts"] = np.asarray(pts_ptrs, dtype=np.uint64)
+    desc["tile0"] = np.concatenate([[0], np.cumsum(tiles)[:-1]]).astype(np.uint64) if cnt else []
+    desc["seed"] = np.asarray(seeds, dtype=np.uint64)
+    desc["n"] = nn.astype(np.uint32)
+    desc["kind"] = np.asarray(kinds, dtype=np.uint32)
+    desc["d"] = d
+    return desc, int(tiles.sum())
+
+
+def device_requests(desc_dev_ptr: int, count: int, total_tiles: int, stream: int = 0) -> None:
+    """One launch that writes every described request's W into its slot
+    (descriptors already in device memory)."""
+    rc = _cuda_lib().synth_cuda_requests(desc_dev_ptr, count, total_tiles, stream)
+    if rc != 0:
+        raise RuntimeError(f"synth_cuda_requests failed: {rc}")
 
 
 def device_uniform01(seed: int, n: int, W_dev_ptr: int, stream: int = 0) -> None:

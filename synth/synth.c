@@ -11,6 +11,9 @@
  *    FP64 in ascending k, each subtraction, square and sum rounded separately
  *    (no fused multiply-add), a correctly rounded square root, then rounded to
  *    FP32.  Only i<j is computed; (j,i) is a copy; the diagonal is +0.0.
+ *  - FP32-arithmetic Euclidean weights (the serving mix's point requests):
+ *    s = 0, then for k ascending t = x_lo,k - x_hi,k and s = fma(t, t, s),
+ *    every step rounded to FP32, and d = sqrt(s) correctly rounded in FP32.
  *  - Hashed weights: h(seed,lo,hi) = mix(mix(seed) ^ (lo<<32 | hi)), where mix
  *    is the SplitMix64 finaliser (Steele, Lea, Flood 2014).  uint32 weights
  *    are h & 0xFFFF; uniform(0,1) FP32 weights are ((h>>40)+0.5)*2^-24
@@ -47,13 +50,23 @@ static float euclid_pair(const float *pts, int d, int64_t i, int64_t j)
     return (float)sqrt(s);
 }
 
+static float euclid32_pair(const float *pts, int d, int64_t i, int64_t j)
+{
+    float s = 0.0f;
+    for (int k = 0; k < d; ++k) {
+        const float t = pts[i * d + k] - pts[j * d + k];
+        s = fmaf(t, t, s);
+    }
+    return sqrtf(s);
+}
+
 typedef struct {
     const float *pts;
     int64_t n;
     int d;
     float *W;
     int64_t r0, r1;
-    int kind;       /* 0 euclid, 1 hash-u32, 2 uniform01 */
+    int kind;       /* 0 euclid, 1 hash-u32, 2 uniform01, 3 euclid in FP32 arithmetic */
     uint64_t seed;
 } job;
 
@@ -72,6 +85,8 @@ static void fill_rows(const job *jb)
             int64_t lo = i < j ? i : j, hi = i < j ? j : i;
             if (jb->kind == 0) {
                 jb->W[i * n + j] = euclid_pair(jb->pts, jb->d, lo, hi);
+            } else if (jb->kind == 3) {
+                jb->W[i * n + j] = euclid32_pair(jb->pts, jb->d, lo, hi);
             } else {
                 uint64_t h = synth_hash(jb->seed, (uint64_t)lo, (uint64_t)hi);
                 if (jb->kind == 1)
@@ -123,6 +138,11 @@ static int run(const float *pts, int64_t n, int d, float *W, int kind, uint64_t 
 int synth_euclid_f32(const float *pts, int64_t n, int d, float *W, int nthreads)
 {
     return run(pts, n, d, W, 0, 0, nthreads);
+}
+
+int synth_euclid32_f32(const float *pts, int64_t n, int d, float *W, int nthreads)
+{
+    return run(pts, n, d, W, 3, 0, nthreads);
 }
 
 int synth_hash_u32(uint64_t seed, int64_t n, uint32_t *W, int nthreads)

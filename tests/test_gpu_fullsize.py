@@ -1,15 +1,16 @@
 """Parity at the full sizes, in the launch configuration the benchmark times.
 
-The single solve runs at n = 65536 (the largest size the library takes) on the
-benchmark's input, built on the device by the same generator and solved with
-the same call on the same stream.  Its n^2 outputs are checked on sampled rows
-that the oracle computes one by one: Prim's tree under the packed edge order
-(unique, so it must equal the device's Boruvka edge set) and one walk of that
-tree per sampled source, whose running maximum is the minimax distance
-(Theorem 1: the minimax path lies on any minimum spanning tree).  Symmetry and
-the zero diagonal are checked on the whole matrix, so sampled rows are sampled
-columns too.  The batch of 4096 small graphs is checked graph by graph on a
-sample that includes the largest and smallest graphs.
+The single solve runs at n = 65536 (the benchmark's size) on the benchmark's
+input, built on the device by the same generator and solved with the same
+call on the same stream.  Every one of its n^2 outputs is compared with the
+oracle: all rows are read off Prim's visiting order (oracle.prim_rows, O(n)
+per row; pinned against the Algorithm 4 matrix and threshold connectivity),
+streamed from the device in blocks of rows.  Prim's tree under the packed
+edge order is unique, so it must also equal the device's Boruvka edge set,
+and a sample of rows is checked once more by walking the tree
+(oracle.tree_rows).  The widest-path order (Section 4.2) is checked the same
+way on the mixture input.  The batch of 4096 small graphs is checked graph by
+graph against the Algorithm 4 oracle, every graph.
 """
 import numpy as np
 import pytest
@@ -23,6 +24,7 @@ from tests.test_gpu_parity import assert_bits
 pytestmark = pytest.mark.gpu
 
 N_FULL = 65536
+ROW_BLOCK = 4096
 
 
 def _device_input(kind: str, n: int) -> torch.Tensor:
@@ -38,14 +40,23 @@ def _device_input(kind: str, n: int) -> torch.Tensor:
     return W
 
 
-@pytest.mark.parametrize("kind", ["gmm16", "u32"])
-def test_full_size_single_solve_sampled_rows(kind):
+def _check_all_rows(M: torch.Tensor, Wh: np.ndarray, order, mst, widest: bool, what: str):
+    n = Wh.shape[0]
+    for r0 in range(0, n, ROW_BLOCK):
+        r1 = min(n, r0 + ROW_BLOCK)
+        ref = oracle.prim_rows(Wh, order, mst, np.arange(r0, r1), widest=widest)
+        got = M[r0:r1].cpu().numpy().view(ref.dtype)
+        assert_bits(got, ref, f"{what} rows {r0}..{r1 - 1}")
+
+
+@pytest.mark.parametrize("kind,widest", [("gmm16", False), ("u32", False), ("gmm16", True)])
+def test_full_size_single_solve_every_row(kind, widest):
     n = N_FULL
     W = _device_input(kind, n)
     M = torch.empty_like(W)
     for _ in range(2):                       # second solve reuses the workspace, as timed
-        appd.solve(W, out=M)
-    E = appd.mst(W)
+        appd.solve(W, out=M, widest=widest)
+    E = appd.mst(W, widest=widest)
     torch.cuda.synchronize()
     assert appd.last_device_status() == 0
     assert appd.check_symmetric(M)
@@ -54,18 +65,20 @@ def test_full_size_single_solve_sampled_rows(kind):
     Wh = W.cpu().numpy()
     if kind == "u32":
         Wh = Wh.view(np.uint32)
-    _, mst_ref = oracle.prim(Wh)
+    order, mst_ref = oracle.prim(Wh, widest=widest)
     got_edges = np.sort(E.cpu().numpy().view(np.uint64))
     assert np.array_equal(got_edges, np.sort(mst_ref)), "MST edge sets differ"
 
+    what = f"n={n} {kind}{' widest' if widest else ''}"
     rng = np.random.default_rng(65536)
-    rows = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1], rng.integers(0, n, 59)]))
-    ref = oracle.tree_rows(Wh, mst_ref, rows)
+    rows = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1], rng.integers(0, n, 27)]))
+    ref = oracle.tree_rows(Wh, mst_ref, rows, widest=widest)
     got = M[torch.from_numpy(rows.astype(np.int64)).cuda()].cpu().numpy().view(ref.dtype)
-    assert_bits(got, ref, f"n={n} {kind} sampled rows")
+    assert_bits(got, ref, f"{what} sampled rows (tree walk)")
+    _check_all_rows(M, Wh, order, mst_ref, widest, what)
 
 
-def test_full_batch_sampled_graphs():
+def test_full_batch_every_graph():
     sizes = [int(x) for x in synth.cfg4_sizes(4096)]
     offs = np.cumsum([0] + [n * n for n in sizes])[:-1].astype(np.int64)
     total = int(offs[-1] + sizes[-1] ** 2)
@@ -78,11 +91,9 @@ def test_full_batch_sampled_graphs():
         appd.solve_batched(W, offs, sizes, out=M)
     torch.cuda.synchronize()
     assert appd.last_device_status() == 0
-    by_size = np.argsort(sizes, kind="stable")
-    rng = np.random.default_rng(4096)
-    pick = np.unique(np.concatenate([by_size[:4], by_size[-4:], rng.integers(0, len(sizes), 24)]))
-    for g in pick:
-        n, o = sizes[g], int(offs[g])
-        Wg = W[o: o + n * n].view(n, n).cpu().numpy()
-        got = M[o: o + n * n].view(n, n).cpu().numpy()
-        assert_bits(got, oracle.appd(Wg), f"batched graph {g} n={n}")
+    Wh = W.cpu().numpy()
+    Mh = M.cpu().numpy()
+    for g, n in enumerate(sizes):
+        o = int(offs[g])
+        Wg = Wh[o: o + n * n].reshape(n, n)
+        assert_bits(Mh[o: o + n * n].reshape(n, n), oracle.appd(Wg), f"batched graph {g} n={n}")

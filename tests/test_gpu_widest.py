@@ -97,3 +97,8 @@ def test_widest_host_entry_and_noalloc():
     assert rc == 0
     torch.cuda.synchronize()
     assert_bits(from_dev(out, W), ref, "widest noalloc")
+
+
+def test_widest_config2b_n16384_ties():
+    W = synth.hash_u32(16384, seed=synth.CFG2B_SEED)
+    assert_bits(solve_widest(W), oracle.appd(W, widest=True), "widest n=16384 uint32 ties")

@@ -342,3 +342,134 @@ def test_planted_mistakes_are_caught(k):
     assert caught, f"mutation {k} not caught by the pins"
     # and the oracle is correct again afterwards
     assert bits_equal(oracle.appd(Ws[0]), refs[0])
+
+
+# ------------------------------------------------ rows from Prim's order
+@pytest.mark.parametrize("widest", [False, True])
+def test_prim_rows_equal_full_matrix(widest):
+    # every row read off Prim's visiting order equals the Algorithm 4 matrix,
+    # on ties, special values and both dtypes
+    rng = np.random.default_rng(31)
+    cases = [synth.euclid(synth.uniform_points(300, 2, seed=32)), synth.hash_u32(257, seed=33),
+             sym_random(64, rng, np.uint32, "ties"), sym_random(50, rng, np.float32, "ties"),
+             sym_random(2, rng, np.float32), sym_random(1, rng, np.uint32)]
+    pool = np.array([0xFFC00000, 0xFF800000, 0xBF800000, 0x80000000, 0x00000000, 0x3F800000,
+                     0x7F800000, 0x7FC00000], dtype=np.uint32)
+    B = np.triu(pool[rng.integers(0, len(pool), size=(40, 40))], 1)
+    B = B + B.T
+    np.fill_diagonal(B, 0)
+    cases.append(np.ascontiguousarray(B.astype(np.uint32)).view(np.float32))
+    for W in cases:
+        n = W.shape[0]
+        order, mst = oracle.prim(W, widest=widest)
+        rows = oracle.prim_rows(W, order, mst, np.arange(n), widest=widest)
+        assert bits_equal(rows, oracle.appd(W, widest=widest)), f"n={n}"
+
+
+def test_prim_rows_vs_threshold_connectivity():
+    rng = np.random.default_rng(34)
+    for W in (sym_random(12, rng, np.uint32, "ties"), sym_random(15, rng, np.float32)):
+        order, mst = oracle.prim(W)
+        rows = oracle.prim_rows(W, order, mst, np.arange(W.shape[0]))
+        assert bits_equal(rows, threshold_connectivity(W))
+
+
+def test_prim_rows_planted_mistake_is_caught():
+    W = synth.euclid(synth.uniform_points(60, 2, seed=35))
+    order, mst = oracle.prim(W)
+    ref = threshold_connectivity(W)
+    with oracle.mutation(5):
+        bad = oracle.prim_rows(W, order, mst, np.arange(60))
+    assert not bits_equal(bad, ref)
+    assert bits_equal(oracle.prim_rows(W, order, mst, np.arange(60)), ref)
+
+
+# ----------------------------------------- FP32 weights of a point set
+def _round_f32(x) -> np.float32:
+    """Round an exact rational to the nearest FP32 value, ties to even."""
+    from fractions import Fraction
+    x = Fraction(x)
+    if x == 0:
+        return np.float32(0.0)
+    sign = -1 if x < 0 else 1
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    e = max(e, -126)                       # subnormals share the smallest exponent
+    scale = Fraction(2) ** (23 - e)
+    m = a * scale
+    q, r = divmod(m.numerator, m.denominator)
+    twice = 2 * r
+    if twice > m.denominator or (twice == m.denominator and q % 2 == 1):
+        q += 1
+    return np.float32(sign * float(Fraction(q) / scale))
+
+
+def _sqrt_f32(s: np.float32) -> np.float32:
+    """Correctly rounded FP32 square root, decided with exact rationals."""
+    import math
+    from fractions import Fraction
+    if s == 0:
+        return np.float32(0.0)
+    S = Fraction(float(s))
+    r = np.float32(math.sqrt(float(s)))
+    for c in (np.nextafter(r, np.float32(0)), r, np.nextafter(r, np.float32(np.inf))):
+        lo = (Fraction(float(np.nextafter(c, np.float32(0)))) + Fraction(float(c))) / 2
+        hi = (Fraction(float(c)) + Fraction(float(np.nextafter(c, np.float32(np.inf))))) / 2
+        if lo * lo <= S <= hi * hi:
+            return c
+    raise AssertionError("no correctly rounded candidate")
+
+
+def _points_w_exact(X: np.ndarray) -> np.ndarray:
+    """Each step of the definition with exact rationals and one rounding."""
+    from fractions import Fraction
+    n, d = X.shape
+    W = np.zeros((n, n), dtype=np.float32)
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            s = np.float32(0.0)
+            for k in range(d):
+                t = _round_f32(Fraction(float(X[i, k])) - Fraction(float(X[j, k])))
+                s = _round_f32(Fraction(float(t)) * Fraction(float(t)) + Fraction(float(s)))
+            W[i, j] = _sqrt_f32(s)
+    return W
+
+
+def test_points_w_vs_exact_rational_steps():
+    for X in (synth.gmm_points(9, 16, 3, sigma=1.0, seed=36, mean_std=5.0),
+              synth.uniform_points(12, 2, seed=37),
+              synth.gmm_points(7, 3, 2, sigma=1e-3, seed=38, mean_box=1e4)):
+        assert bits_equal(oracle.points_w(X), _points_w_exact(X))
+
+
+def test_points_w_vs_numpy_where_products_are_exact():
+    # coordinates on a grid of 2^-6 with small integer parts: every difference
+    # has at most 12 significant bits, so t*t is exact in FP32 and the fused
+    # step equals numpy's float32 multiply then add in the same order
+    rng = np.random.default_rng(39)
+    X = (rng.integers(-2000, 2000, size=(40, 5)) / 64.0).astype(np.float32)
+    n, d = X.shape
+    ref = np.zeros((n, n), dtype=np.float32)
+    for i in range(n):
+        s = np.zeros(n, dtype=np.float32)
+        for k in range(d):
+            t = (X[i, k] - X[:, k]).astype(np.float32)
+            s = (s + (t * t).astype(np.float32)).astype(np.float32)
+        ref[i] = np.sqrt(s).astype(np.float32)
+    np.fill_diagonal(ref, 0)
+    assert bits_equal(oracle.points_w(X), ref)
+
+
+def test_points_w_vs_fp64_generator_on_integer_points():
+    # integer coordinates: every step is exact in both, so the FP32 definition
+    # and the FP64-then-rounded generator agree
+    rng = np.random.default_rng(40)
+    X = rng.integers(-300, 300, size=(64, 16)).astype(np.float32)
+    W = oracle.points_w(X)
+    assert bits_equal(W, synth.euclid(X))
+    assert bits_equal(W, np.ascontiguousarray(W.T))
+    assert not np.any(np.diag(W).view(np.uint32))

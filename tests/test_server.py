@@ -149,3 +149,40 @@ def test_server_argument_errors_need_no_gpu():
     assert lib.appd_server_commit_many(None, 1, None, None) == 1
     assert lib.appd_server_release_many(None, 1, None, None) == 1
     assert lib.appd_server_destroy(None) == 1
+
+
+@pytest.mark.gpu
+def test_served_mix_every_result_matches_oracle():
+    """300 requests of the serving mix (20000-request stream, n log-uniform in
+    [64, 8192], half FP32 point distances, half uint32 ties), including its
+    largest graphs, driven by the benchmark's own loop: bursts of 30 requests
+    every 2 ms under the 40 GB budget, so admission, generation and solves of
+    different groups overlap on the device.  Every result is compared with
+    the oracle (rows read off Prim's order), before its slot is released."""
+    import bench
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ns, dts = bench.serving_requests(20000)
+    big = np.argsort(ns, kind="stable")[-20:]
+    idx = np.unique(np.concatenate([np.arange(280), big]))
+    assert ns[idx].max() == 8192 and set(dts[idx].tolist()) == {0, 1}
+    inp = bench.ServingInputs(ns, dts, dev)
+    arrivals = (np.arange(len(idx)) // 30) * 0.002
+    bad = []
+
+    def on_done(k, ptr):
+        n = int(ns[k])
+        W = inp.host_matrix(k)
+        got = appd.device_view(ptr, n, appd.U32 if dts[k] else appd.F32).cpu().numpy()
+        order, mst = oracle.prim(W)
+        ref = oracle.prim_rows(W, order, mst, np.arange(n))
+        if not np.array_equal(got.view(np.uint32), ref.view(np.uint32)):
+            bad.append((k, n))
+
+    sv = appd.Server(40 << 30, 8192)
+    try:
+        lat, _, _ = bench.run_serving(sv, inp, idx, arrivals, dev, on_done)
+    finally:
+        sv.close()
+    assert appd.last_device_status() == 0
+    assert not bad, f"requests differing from the oracle: {bad[:10]}"
+    assert np.all(lat > 0)
