@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-insert", action="store_true")
     p.add_argument("--no-configs", action="store_true")
+    p.add_argument("--no-points", action="store_true")
     return p.parse_args()
 
 
@@ -242,6 +243,74 @@ def bench_configs(dev, peak: float, reps: int = 10):
             raise RuntimeError(f"device status error in {name}")
         out[name] = ent
         del W, M
+        torch.cuda.empty_cache()
+    return out
+
+
+def alu_peak_ops(dev) -> float:
+    """FP32 lane operations per second at the maximum SM clock: SMs x 128
+    FP32 lanes x clock (one add or one fused multiply-add per lane per cycle)."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return props.multi_processor_count * 128 * mhz * 1e6
+
+
+def bench_points(dev, peak: float, reps: int = 10):
+    """The point-set solve (appd_solve_points: W computed where it is used,
+    never stored): median device time per solve, phase times, the M write as
+    a fraction of the HBM peak, and the two distance passes (round-1 minima
+    and level-0 contraction, 2 d FP32 operations per pair and pass over the
+    upper triangle) as a fraction of the FP32 ALU peak."""
+    import torch
+
+    import synth
+    from paper_2407_07058_gb300 import appd
+    st = torch.cuda.current_stream()
+    alu = alu_peak_ops(dev)
+    cases = [("gmm16_n65536", synth.cfg3_points(65536),
+              "n=65536 16-D points, 32-component mixture (the n=65536 workload's points)"),
+             ("uniform2_n65536", synth.uniform_points(65536, 2, seed=2),
+              "n=65536 2-D points uniform in [0,1]^2"),
+             ("uniform2_n16384", synth.cfg2a_points(),
+              "n=16384 2-D points uniform in [0,1]^2 (the n=16384 workload's points)")]
+    out = {}
+    for name, X, desc in cases:
+        n, d = X.shape
+        T = torch.from_numpy(X).to(dev)
+        M = torch.empty((n, n), dtype=torch.float32, device=dev)
+        for _ in range(3):
+            appd.solve_points(T, out=M)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            appd.solve_points(T, out=M)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        appd.profile_begin()
+        for _ in range(reps):
+            appd.solve_points(T, out=M)
+        prof = appd.profile_end()
+        if appd.last_device_status() != 0:
+            raise RuntimeError(f"device status error in points {name}")
+        ms = statistics.median(times)
+        ph = {k: prof[k] / reps for k in appd.PHASES[:6]}
+        pairs = n * (n - 1) / 2.0
+        ops = 2.0 * d * pairs
+        out[name] = {"workload": desc, "ms": ms, "entries_per_s": n * n / (ms / 1e3),
+                     "phases_ms": ph,
+                     "hbm_frac_m_write": (4.0 * n * n + 4.0 * n * d) / (ms / 1e3) / 1e9 / peak,
+                     "rowmin_alu_frac": ops / (ph["rowmin"] / 1e3) / alu if ph["rowmin"] > 0 else None,
+                     "contract0_alu_frac": ops / (ph["contract_w"] / 1e3) / alu if ph["contract_w"] > 0 else None,
+                     "alu_peak_lane_ops_per_s": alu}
+        del T, M
         torch.cuda.empty_cache()
     return out
 
@@ -708,6 +777,11 @@ def run_ours(args, rank, world, local):
         del W, M
         torch.cuda.empty_cache()
         configs = bench_configs(dev, peak)
+    points = None
+    if not args.no_points:
+        W = M = None
+        torch.cuda.empty_cache()
+        points = bench_points(dev, peak)
     batched = None
     if not args.no_batched:
         W = M = None
@@ -738,6 +812,7 @@ def run_ours(args, rank, world, local):
             "hbm_frac_solve_min_bytes": min_frac, "hbm_frac_solve_w_plus_m": wm_frac,
             "insert": insert,
             "configs": configs,
+            "points": points,
             "batched": batched,
             "serving": serving,
         }

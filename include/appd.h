@@ -104,6 +104,27 @@ const char *appd_status_str(appd_status st);
 appd_status appd_solve(const void *W, int64_t n, appd_dtype dt, void *M, appd_stream_t s);
 
 /*
+ * appd_solve_points -- the APPD matrix of a point set's complete graph
+ * (Section 1 turns a dataset into a complete graph; Section 4's experiments
+ * use point datasets) without forming W: the edge weights are computed where
+ * the MST reads them, so device memory holds only the points and M.
+ *   X   device pointer, n x d FP32 coordinates, row-major (4-byte aligned).
+ *   n   number of points; d dimensions, 1 <= d <= 32.
+ *   dt  APPD_F32 (minimax) or APPD_F32_WIDEST (widest paths, Section 4.2).
+ *   M   device pointer, n x n FP32, receives the result; must not overlap X
+ *       (APPD_ERR_ALIAS).
+ * The edge weight is the Euclidean distance evaluated in FP32 in a fixed
+ * order: s = 0, then for k = 0 .. d-1, t = X(i,k) - X(j,k) rounded to FP32
+ * and s = fma(t, t, s) with one rounding; W(i,j) = sqrt(s), correctly
+ * rounded; W(i,i) = +0.  The result is bit-identical to appd_solve on the
+ * matrix W so defined.  Coordinates must be finite.  The library keeps a
+ * padded copy of the coordinates in its workspace (n x 32 floats at most).
+ * 0 <= n <= 65536; other conventions as appd_solve.
+ */
+appd_status appd_solve_points(const float *X, int64_t n, int32_t d, appd_dtype dt, void *M,
+                              appd_stream_t s);
+
+/*
  * appd_solve_alg4 -- same result as appd_solve, but M is written by a GPU
  * form of Algorithm 4's calculation-and-copy step (Sections 3, 5 and the
  * parallel variant of Section 6.2): one work item per MST edge e fills the

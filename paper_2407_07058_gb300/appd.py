@@ -24,7 +24,7 @@ STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD
           8: "APPD_ERR_ALIAS", 9: "APPD_ERR_NOT_FOUND", 10: "APPD_ERR_INTERNAL"}
 
 # every symbol that include/appd.h declares
-EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_alg4", "appd_solve_host",
+EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_points", "appd_solve_alg4", "appd_solve_host",
            "appd_solve_host_async", "appd_solve_host_wait", "appd_solve_noalloc", "appd_insert_vertex", "appd_mst", "appd_leaf_order",
            "appd_solve_batched", "appd_batched_tuning", "appd_batched_autotune",
            "appd_batched_get_tuning", "appd_check_symmetric",
@@ -58,6 +58,7 @@ def load(build_if_missing: bool = True):
         ci = ctypes.c_int
         sig = {
             "appd_solve": [vp, i64, ci, vp, vp],
+            "appd_solve_points": [vp, i64, i32, ci, vp, vp],
             "appd_solve_alg4": [vp, i64, ci, vp, vp],
             "appd_solve_host": [vp, i64, ci, vp, vp],
             "appd_solve_host_async": [vp, i64, ci, vp, vp],
@@ -140,6 +141,23 @@ def solve(W, out=None, stream=None, alg4: bool = False, widest: bool = False):
     fn = load().appd_solve_alg4 if alg4 else load().appd_solve
     with torch.cuda.device(W.device):
         _check(fn(W.data_ptr(), n, dt, M.data_ptr(), _stream_ptr(stream)), "appd_solve")
+    return M
+
+
+def solve_points(X, out=None, stream=None, widest: bool = False):
+    """APPD matrix of the complete graph of the points X (n x d FP32, CUDA),
+    edge weights computed on the fly in FP32 (see appd.h); returns M (n x n)."""
+    import torch
+    if not X.is_cuda:
+        raise ValueError("X must be a CUDA tensor (no CPU path)")
+    if X.dim() != 2 or X.dtype != torch.float32 or not X.is_contiguous():
+        raise ValueError("X must be a contiguous n x d float32 matrix")
+    n, d = X.shape
+    M = torch.empty((n, n), dtype=torch.float32, device=X.device) if out is None else out
+    dt = F32 | (WIDEST if widest else 0)
+    with torch.cuda.device(X.device):
+        _check(load().appd_solve_points(X.data_ptr(), n, d, dt, M.data_ptr(), _stream_ptr(stream)),
+               "appd_solve_points")
     return M
 
 

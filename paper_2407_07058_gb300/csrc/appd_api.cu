@@ -133,6 +133,7 @@ cudaError_t appd::workspace_create(int64_t n, Workspace** out)
     nw->bin_cap = (u32)((smem_optin - 2048) / 8);
     nw->bin_cap2 = (u32)((smem_optin / 2 - 2048) / 8);
     nw->bin_cap_t = contract_tma_bin_cap(smem_optin);
+    nw->bin_cap_p = contract_pts_bin_cap(smem_optin);
     *out = nw;
     return cudaSuccess;
 }
@@ -144,6 +145,7 @@ void appd::workspace_destroy(Workspace* w)
     cudaDeviceSynchronize();
     cudaFree(w->base);
     cudaFree(w->cscratch);
+    cudaFree(w->pscratch);
     cudaFree(w->hostW);
     cudaFree(w->hostM);
     delete w;
@@ -449,6 +451,67 @@ const char* appd_status_str(appd_status st)
 appd_status appd_solve(const void* W, int64_t n, appd_dtype dt, void* M, appd_stream_t s)
 {
     return solve_impl(W, n, (int)dt, M, (cudaStream_t)s, false);
+}
+
+appd_status appd_solve_points(const float* X, int64_t n, int32_t d, appd_dtype dt, void* M,
+                              appd_stream_t s)
+{
+    if (n < 0 || !X || !M || (dt != APPD_F32 && dt != APPD_F32_WIDEST) || points_dim(d) == 0)
+        return APPD_ERR_INVALID;
+    if (n > 65536)
+        return APPD_ERR_TOO_LARGE;
+    {
+        const char* a = (const char*)X;
+        const char* b = (const char*)M;
+        const size_t xb = (size_t)n * (size_t)d * 4, mb = (size_t)n * (size_t)n * 4;
+        if (a < b + mb && b < a + xb)
+            return APPD_ERR_ALIAS;
+    }
+    if (n == 0)
+        return APPD_OK;
+    cudaStream_t cs = (cudaStream_t)s;
+    std::lock_guard<std::mutex> lk(g_mu);
+    SolveCtx c;
+    appd_status st;
+    if ((st = prepare(n, c)) != APPD_OK)
+        return st;
+    Workspace& w = *c.ws;
+    const int D = points_dim(d);
+    const size_t need = (size_t)points_rows_padded((u32)n) * D * sizeof(float);
+    if (w.pscratch_bytes < need) {
+        cudaDeviceSynchronize();
+        cudaFree(w.pscratch);
+        w.pscratch = nullptr;
+        w.pscratch_bytes = 0;
+        // sized for the workspace's capacity at 32 dimensions, so that it is
+        // allocated once
+        const size_t full = (size_t)points_rows_padded((u32)w.cap) * 32 * sizeof(float);
+        cudaError_t e = cudaMalloc(&w.pscratch, full);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        w.pscratch_bytes = full;
+    }
+    cudaError_t e = launch_pts_pad(X, (u32)n, d, w.pscratch, cs);
+    prof_launches(1);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    set_sizes(w, n);
+    g_last_ctr = w.ctr;
+    const PointsSrc ps{w.pscratch, D};
+    e = run_mst(w, nullptr, (int)dt, M, contraction_scratch_bytes(n), c.status, cs, &ps);
+    if (e == cudaSuccess) {
+        prof_begin(PH_LEAF, cs);
+        e = run_leaf_order(w, c.status, cs);
+        prof_end(PH_LEAF, cs);
+        prof_launches(1);
+    }
+    if (e == cudaSuccess) {
+        prof_begin(PH_FILL, cs);
+        e = run_fill(w, (int)dt, M, cs);
+        prof_end(PH_FILL, cs);
+        prof_launches(1);
+    }
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
 }
 
 appd_status appd_solve_alg4(const void* W, int64_t n, appd_dtype dt, void* M, appd_stream_t s)

@@ -45,6 +45,7 @@ struct Workspace {
     u32 bin_cap = 0;         // u64 bins per contraction CTA (one CTA per SM)
     u32 bin_cap2 = 0;        // u64 bins per contraction CTA (two CTAs per SM)
     u32 bin_cap_t = 0;       // u64 bins beside the copy ring of the bulk-copy contraction
+    u32 bin_cap_p = 0;       // u64 bins of the point-set contraction (one CTA per SM)
     void* base = nullptr;
     size_t bytes = 0;
 
@@ -74,15 +75,37 @@ struct Workspace {
     // contraction matrices when M cannot serve as scratch (M == W)
     void* cscratch = nullptr;
     size_t cscratch_bytes = 0;
+    // zero-padded coordinates of a point-set solve (appd_solve_points)
+    float* pscratch = nullptr;
+    size_t pscratch_bytes = 0;
     // staging for appd_solve_host
     void* hostW = nullptr;
     void* hostM = nullptr;
     size_t host_bytes = 0;
 };
 
-// launch sequence pieces (all asynchronous on the stream)
+// A point set in place of W (points.cu): P holds n_pad x D zero-padded FP32
+// coordinates; the edge weights are computed where they are used.
+struct PointsSrc {
+    const float* P;
+    int D;
+};
+// padded dimension (2, 4, 8, 16 or 32) of a d-dimensional set, 0 if d is out of range
+int points_dim(int d);
+u32 points_rows_padded(u32 n);
+cudaError_t launch_pts_pad(const float* X, u32 n, int d, float* P, cudaStream_t s);
+cudaError_t launch_rowmin_pts(const float* P, int D, u32 n, int dt, u64* best, cudaStream_t s);
+u32 contract_pts_bin_cap(int smem_optin);
+struct ContractArgs;
+cudaError_t launch_contract_pts(const ContractArgs& ca, const float* P, int D, int dt, int blocks,
+                                cudaStream_t s);
+cudaError_t launch_mst_sqrt(u64* mst, u32 m, int dt, cudaStream_t s);
+cudaError_t preload_points();
+
+// launch sequence pieces (all asynchronous on the stream); with ps, the
+// graph is the point set's and W is not read
 cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbuf_bytes,
-                    u32* status, cudaStream_t s);
+                    u32* status, cudaStream_t s, const PointsSrc* ps = nullptr);
 cudaError_t run_leaf_order(Workspace& ws, u32* status, cudaStream_t s);
 cudaError_t run_fill(Workspace& ws, int dt, void* M, cudaStream_t s);
 cudaError_t run_fill_alg4(Workspace& ws, int dt, void* M, u32* status, cudaStream_t s);

@@ -384,6 +384,8 @@ cudaError_t preload_kernels()
         e = preload_fill();
     if (e == cudaSuccess)
         e = preload_batched();
+    if (e == cudaSuccess)
+        e = preload_points();
     return e;
 }
 
@@ -394,7 +396,7 @@ size_t contraction_scratch_bytes(int64_t n)
 }
 
 cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbuf_bytes,
-                    u32* status, cudaStream_t s)
+                    u32* status, cudaStream_t s, const PointsSrc* ps)
 {
     const u32 n = (u32)ws.n;
     cudaError_t err;
@@ -404,10 +406,18 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         return err;
     if (n <= 1)
         return cudaSuccess;
-    const bool vec = (n % 4 == 0) && ((uintptr_t)W % 16 == 0);
+    // vec: rows of W 16-byte aligned (upper-triangle passes over W);
+    // upper: level 0 leaves the unsymmetrized P (stored W with vec, or points)
+    const bool vec = !ps && (n % 4 == 0) && ((uintptr_t)W % 16 == 0);
+    const bool upper = vec || ps;
     prof_launches(1);
     prof_begin(PH_ROWMIN, s);
-    if (vec) {
+    if (ps) {
+        if ((err = cudaMemsetAsync(ws.best[0], 0xFF, (size_t)n * sizeof(u64), s)) != cudaSuccess)
+            return err;
+        if ((err = launch_rowmin_pts(ps->P, ps->D, n, dt, ws.best[0], s)) != cudaSuccess)
+            return err;
+    } else if (vec) {
         // upper-triangle tiles; best[] is reduced with atomic minima from +inf
         if ((err = cudaMemsetAsync(ws.best[0], 0xFF, (size_t)n * sizeof(u64), s)) != cudaSuccess)
             return err;
@@ -477,7 +487,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         sa.part = ws.part;
         sa.ctr = ws.ctr;
         sa.status = status;
-        sa.bin_cap = ws.bin_cap;
+        sa.bin_cap = (r == 0 && ps) ? ws.bin_cap_p : ws.bin_cap;
         // level 0 of the upper-triangle path also keeps 16-bit labels (every
         // component of round 1 has two or more vertices: ids < 32768)
         sa.label16 = (r == 0 && vec && ws.bin_cap_t > 0) ? ws.label16 : nullptr;
@@ -521,7 +531,13 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         prof_begin(ph, s);
         ContractArgs ca1 = ca;
         ca.bin_cap = ws.bin_cap2;
-        if (r == 0 && vec && ws.bin_cap_t > 0) {
+        if (r == 0 && ps) {
+            // the point set's level 0: every distance computed once per bin range
+            ContractArgs cap = ca;
+            cap.bin_cap = ws.bin_cap_p;
+            if ((err = launch_contract_pts(cap, ps->P, ps->D, dt, ws.contract_blocks, s)) != cudaSuccess)
+                return err;
+        } else if (r == 0 && vec && ws.bin_cap_t > 0) {
             // upper triangle streamed by bulk copies while |C_1| fits beside
             // the copy ring, else one CTA per SM with all bins
             ContractArgs cat = ca;
@@ -539,14 +555,14 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         } else {
             k1<<<2 * ws.contract_blocks, CONTRACT_THREADS2, smem2, s>>>(ca, 0u, 0xFFFFFFFFu);
         }
-        if (vec && r == 0) {
+        if (upper && r == 0) {
             // C_1's row minima also take P's column minima
             prof_launches(1);
             const u32 g = (u32)((h + CMIN_THREADS - 1) / CMIN_THREADS);
             const u32 gy = (u32)((h + CMIN_ROWS - 1) / CMIN_ROWS);
             k_colmin_p<<<dim3(g, gy), CMIN_THREADS, 0, s>>>(cb[0], ws.ctr, ws.best[1]);
         }
-        if (vec && r == 1) {
+        if (upper && r == 1) {
             // level 1 contracted the unsymmetrized P: symmetrize C_2
             prof_launches(1);
             k_sym<<<ws.sms * 3, SYM_THREADS, sym_smem_bytes(), s>>>(cb[1], ws.ctr, 1, ws.best[0]);
@@ -555,6 +571,9 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         if ((err = cudaGetLastError()) != cudaSuccess)
             return err;
     }
+    // the point set's tree carries keys of squared distances: convert them
+    if (ps)
+        return launch_mst_sqrt(ws.mst, n - 1, dt, s);
     return cudaSuccess;
 }
 

