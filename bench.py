@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-insert", action="store_true")
     p.add_argument("--no-configs", action="store_true")
     p.add_argument("--no-points", action="store_true")
+    p.add_argument("--no-wide", action="store_true")
     return p.parse_args()
 
 
@@ -312,6 +313,49 @@ def bench_points(dev, peak: float, reps: int = 10):
                      "alu_peak_lane_ops_per_s": alu}
         del T, M
         torch.cuda.empty_cache()
+    return out
+
+
+def bench_wide(dev, peak: float, reps: int = 5, n: int = 92680):
+    """A solve above 65536 vertices, near the largest the packed edges allow
+    (92682; 92680 keeps rows 16-byte aligned): FP32 distances of 16-D
+    mixture points, W and M 34.4 GB each; median device time per solve,
+    phases, W-read-plus-M-write fraction."""
+    import torch
+
+    import synth
+    from paper_2407_07058_gb300 import appd
+    st = torch.cuda.current_stream()
+    pts = torch.from_numpy(synth.gmm_points(n, 16, 32, sigma=1.0, seed=4, mean_std=5.0)).to(dev)
+    W = torch.empty((n, n), dtype=torch.float32, device=dev)
+    synth.device_euclid(pts.data_ptr(), n, 16, W.data_ptr(), st.cuda_stream)
+    del pts
+    M = torch.empty_like(W)
+    for _ in range(2):
+        appd.solve(W, out=M)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        appd.solve(W, out=M)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    appd.profile_begin()
+    for _ in range(reps):
+        appd.solve(W, out=M)
+    prof = appd.profile_end()
+    if appd.last_device_status() != 0:
+        raise RuntimeError(f"device status error in the n={n} solve")
+    ms = statistics.median(times)
+    out = {"workload": f"single solve n={n}, FP32 Euclidean distances of 16-D points, "
+                       "32-component Gaussian mixture (W and M 34.4 GB each)",
+           "n": n, "ms": ms, "entries_per_s": n * n / (ms / 1e3),
+           "hbm_frac_w_plus_m": 8.0 * n * n / (ms / 1e3) / 1e9 / peak,
+           "phases_ms": {k: prof[k] / reps for k in appd.PHASES[:6]}, "c1": prof["c1"]}
+    del W, M
+    torch.cuda.empty_cache()
     return out
 
 
@@ -730,12 +774,33 @@ def run_ours(args, rank, world, local):
             raise RuntimeError("device status error in the insertion run")
         ms_i = ev0.elapsed_time(ev1) / ki
         ib = 8.0 * n * n + 4.0 * (n + 1) * (n + 1)   # M read twice, M' written
-        insert = {"workload": f"insert one vertex into the solved n={n} matrix",
-                  "ms": ms_i, "entries_per_s": (n + 1) * (n + 1) / (ms_i / 1e3),
-                  "algorithmic_bytes": ib, "achieved_gbs": ib / (ms_i / 1e3) / 1e9,
-                  "frac_of_peak": ib / (ms_i / 1e3) / 1e9 / peak,
+        # the same insertion through the tree (appd_insert_vertex_tree): the
+        # new tree from G's tree and the star of p, leaf order, one fill
+        tree = appd.mst_edges(W)
+        for _ in range(2):
+            appd.insert_vertex_tree(tree, w_new, n, W.dtype, out=Mo, tree_out=False)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(ki):
+            appd.insert_vertex_tree(tree, w_new, n, W.dtype, out=Mo, tree_out=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if appd.last_device_status() != 0:
+            raise RuntimeError("device status error in the tree insertion run")
+        ms_t = ev0.elapsed_time(ev1) / ki
+        tb = 4.0 * (n + 1) * (n + 1)   # M' written; the tree work is O(n log n)
+        insert = {"workload": f"insert one vertex into the solved n={n} graph",
+                  "tree_update": {"api": "appd_insert_vertex_tree (G's tree + p's edges -> "
+                                         "new tree, leaf order, one fill)",
+                                  "ms": ms_t, "entries_per_s": (n + 1) * (n + 1) / (ms_t / 1e3),
+                                  "algorithmic_bytes": tb, "achieved_gbs": tb / (ms_t / 1e3) / 1e9,
+                                  "frac_of_peak": tb / (ms_t / 1e3) / 1e9 / peak},
+                  "from_matrix": {"api": "appd_insert_vertex (two passes over M, M' written)",
+                                  "ms": ms_i, "entries_per_s": (n + 1) * (n + 1) / (ms_i / 1e3),
+                                  "algorithmic_bytes": ib, "achieved_gbs": ib / (ms_i / 1e3) / 1e9,
+                                  "frac_of_peak": ib / (ms_i / 1e3) / 1e9 / peak},
                   "solve_from_scratch_ms": ms_step}
-        del Mo, w_new
+        del Mo, w_new, tree
         torch.cuda.empty_cache()
 
     # ---- end to end through the host entry point (pinned buffers)
@@ -782,6 +847,11 @@ def run_ours(args, rank, world, local):
         W = M = None
         torch.cuda.empty_cache()
         points = bench_points(dev, peak)
+    wide = None
+    if not args.no_wide:
+        W = M = None
+        torch.cuda.empty_cache()
+        wide = bench_wide(dev, peak)
     batched = None
     if not args.no_batched:
         W = M = None
@@ -813,6 +883,7 @@ def run_ours(args, rank, world, local):
             "insert": insert,
             "configs": configs,
             "points": points,
+            "wide": wide,
             "batched": batched,
             "serving": serving,
         }

@@ -31,8 +31,10 @@
  *  - W must be symmetric (undirected graph, Section 1).  Only the upper
  *    triangle is relied on by the specification; results for an asymmetric W
  *    are unspecified.  appd_check_symmetric validates.
- *  - 1 <= n <= 65536 (edge endpoints are packed in 16 bits); n == 0 is a
- *    no-op that returns APPD_OK; n > 65536 returns APPD_ERR_TOO_LARGE.
+ *  - 1 <= n <= 92682 (an edge is packed with its endpoints' pair number in
+ *    32 bits, and n (n - 1) / 2 <= 2^32 there); n == 0 is a no-op that
+ *    returns APPD_OK; larger n returns APPD_ERR_TOO_LARGE.  A solve at the
+ *    limit holds W and M, 2 x 34.4 GB, or M alone in place.
  *  - Device pointers are owned by the caller.  Calls are asynchronous on the
  *    given CUDA stream (cudaStream_t, passed as appd_stream_t; NULL is the
  *    legacy default stream).  Argument errors are returned synchronously
@@ -74,7 +76,7 @@ typedef enum {
 typedef enum {
     APPD_OK = 0,
     APPD_ERR_INVALID = 1,    /* null pointer, n < 0, bad dtype, bad batch layout */
-    APPD_ERR_TOO_LARGE = 2,  /* n > 65536 */
+    APPD_ERR_TOO_LARGE = 2,  /* n above the entry point's limit */
     APPD_ERR_NOMEM = 3,      /* device or host allocation failed */
     APPD_ERR_CUDA = 4,       /* a CUDA runtime call failed */
     APPD_ERR_ASYMMETRIC = 5, /* appd_check_symmetric found W(i,j) != W(j,i) */
@@ -119,7 +121,7 @@ appd_status appd_solve(const void *W, int64_t n, appd_dtype dt, void *M, appd_st
  * rounded; W(i,i) = +0.  The result is bit-identical to appd_solve on the
  * matrix W so defined.  Coordinates must be finite.  The library keeps a
  * padded copy of the coordinates in its workspace (n x 32 floats at most).
- * 0 <= n <= 65536; other conventions as appd_solve.
+ * 0 <= n <= 92682; other conventions as appd_solve.
  */
 appd_status appd_solve_points(const float *X, int64_t n, int32_t d, appd_dtype dt, void *M,
                               appd_stream_t s);
@@ -197,11 +199,36 @@ appd_status appd_solve_noalloc(const void *W, int64_t n, appd_dtype dt, void *M,
  * M_out(i,j) = min(M(i,j), max(d(i), d(j))), M_out(i,n) = M_out(n,i) = d(i),
  * all-zero diagonal; comparisons and the widest dtypes as appd_solve.  The
  * result equals appd_solve on the (n+1)-vertex graph, bit for bit.  Two
- * streaming passes over M.  0 <= n <= 65536 (n == 0: M and w may be NULL,
- * M_out becomes the 1 x 1 zero matrix); n > 65536 returns APPD_ERR_TOO_LARGE.
+ * streaming passes over M.  0 <= n < 92682 (n == 0: M and w may be NULL,
+ * M_out becomes the 1 x 1 zero matrix); larger n returns APPD_ERR_TOO_LARGE.
  */
 appd_status appd_insert_vertex(const void *M, int64_t n, appd_dtype dt, const void *w, void *M_out,
                                appd_stream_t s);
+
+/*
+ * appd_insert_vertex_tree -- warm start (Section 6.1) through the minimum
+ * spanning tree: the matrix of G + p from G's tree and the new vertex's
+ * weights, without reading G's matrix.
+ *   keys, lo, hi  device arrays of n-1 uint32: G's minimum spanning tree as
+ *                 appd_mst_edges returns it (same dtype; order keys).
+ *   w             device, n weights: w[k] = weight of the edge between k and p.
+ *   M_out         device, (n+1) x (n+1): the matrix of G + p, p = vertex n.
+ *   keys_out, lo_out, hi_out  device arrays of n uint32 receiving the tree of
+ *                 G + p (same format), or all three NULL; pass them to the
+ *                 next call to insert vertices one after another.
+ * Every edge of G outside its tree is the largest on a cycle of G, so the
+ * tree of G + p takes only the n-1 tree edges and p's n edges: it is found by
+ * Boruvka's algorithm on those 2n-1 edges (O(n log n) work), followed by the
+ * leaf order and one fill of M_out, the only O(n^2) traffic.  The result
+ * equals appd_solve on the (n+1)-vertex graph, bit for bit, when the tree is
+ * G's minimum spanning tree.  None of the arrays may overlap M_out or the
+ * tree outputs (APPD_ERR_ALIAS).  0 <= n < 92682 (n == 0: M_out becomes the
+ * 1 x 1 zero matrix); dtypes and comparisons as appd_solve.
+ */
+appd_status appd_insert_vertex_tree(const uint32_t *keys, const uint32_t *lo, const uint32_t *hi,
+                                    int64_t n, appd_dtype dt, const void *w, void *M_out,
+                                    uint32_t *keys_out, uint32_t *lo_out, uint32_t *hi_out,
+                                    appd_stream_t s);
 
 /*
  * appd_mst -- the minimum spanning tree computed by the solve's MST stage.
@@ -213,9 +240,18 @@ appd_status appd_insert_vertex(const void *M, int64_t n, appd_dtype dt, const vo
  *              spanning tree).  Edge order in the array is unspecified.
  * Under the strict order (key, lo, hi) the MST is unique, so the edge set can
  * be compared exactly with any correct MST algorithm (Section 3 uses Prim).
+ * 16-bit endpoints: n <= 65536 (APPD_ERR_TOO_LARGE above; see appd_mst_edges).
  */
 appd_status appd_mst(const void *W, int64_t n, appd_dtype dt, uint64_t *edges_out,
                      appd_stream_t s);
+
+/*
+ * appd_mst_edges -- the same tree for any n the library takes, as three
+ * device arrays of n-1 uint32 values: keys[k] (the order key, as appd_mst),
+ * lo[k] < hi[k] (the endpoints).  Edge order unspecified.
+ */
+appd_status appd_mst_edges(const void *W, int64_t n, appd_dtype dt, uint32_t *keys,
+                           uint32_t *lo, uint32_t *hi, appd_stream_t s);
 
 /*
  * appd_leaf_order -- the single-linkage leaf order used by the fill.
@@ -232,7 +268,7 @@ appd_status appd_leaf_order(const void *W, int64_t n, appd_dtype dt, uint32_t *p
  * appd_solve_batched -- many independent graphs in one launch sequence.
  *   offsets  host array, count entries: element offset of graph g in Ws and Ms.
  *   Ws       device base pointer; graph g's W starts at (elem*)Ws + offsets[g].
- *   ns       host array, count entries: n of each graph (1..65536).
+ *   ns       host array, count entries: n of each graph (1..92682).
  *   dts      host array of count bytes (APPD_F32 / APPD_U32) or NULL (all F32).
  *   Ms       device base pointer; graph g's M starts at (elem*)Ms + offsets[g].
  *   count    number of graphs.

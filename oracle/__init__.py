@@ -64,11 +64,14 @@ def _lib():
             lib.appd_oracle_fw.argtypes = [vp, i64, ci, vp]
             lib.appd_oracle_brute.argtypes = [vp, i64, ci, vp]
             lib.appd_oracle_prim.argtypes = [vp, i64, ci, vp, vp]
+            lib.appd_oracle_prim_sym.argtypes = [vp, i64, ci, vp, vp]
             lib.appd_oracle_tree_rows.argtypes = [vp, i64, ci, vp, vp, i64, vp]
             lib.appd_oracle_insert.argtypes = [vp, i64, ci, vp, vp]
             lib.appd_oracle_prim_rows.argtypes = [vp, i64, ci, vp, vp, vp, i64, vp]
             lib.appd_oracle_points_w.argtypes = [vp, i64, ci, vp]
             lib.appd_oracle_set_mutation.argtypes = [ci]
+            lib.appd_oracle_set_short_limit.argtypes = [i64]
+            lib.appd_oracle_code_ends.argtypes = [vp, i64, i64, vp, vp]
             lib.appd_oracle_order_key.argtypes = [ctypes.c_uint32, ci]
             lib.appd_oracle_order_key.restype = ctypes.c_uint32
             _LIB = lib
@@ -127,8 +130,10 @@ def brute(W: np.ndarray, widest: bool = False) -> np.ndarray:
 def prim(W: np.ndarray, widest: bool = False):
     """Return (order, mst_codes): Prim order from vertex 0 and the n-1 edge codes.
 
-    mst_codes[k] = key << 32 | lo << 16 | hi of the edge that added order[k+1]
-    (with widest=True: the maximum spanning tree, key complemented).
+    mst_codes[k] = key << 32 | p of the edge that added order[k+1] (with
+    widest=True: the maximum spanning tree, key complemented), where the pair
+    number p is lo << 16 | hi for n <= 65536 and otherwise the rank of (lo, hi)
+    among all pairs in lexicographic order (see ``code_ends``).
     """
     Wc, n, dt = _prep(W, widest)
     order = np.empty(n, dtype=np.uint32)
@@ -136,6 +141,43 @@ def prim(W: np.ndarray, widest: bool = False):
     _check(_lib().appd_oracle_prim(Wc.ctypes.data, n, dt, mst.ctypes.data, order.ctypes.data),
            "appd_oracle_prim")
     return order, mst[: n - 1]
+
+
+def prim_sym(W: np.ndarray, widest: bool = False):
+    """prim() for a W that is symmetric bit for bit, reading whole rows (the
+    same result; sequential reads for the largest matrices)."""
+    Wc, n, dt = _prep(W, widest)
+    order = np.empty(n, dtype=np.uint32)
+    mst = np.empty(max(n - 1, 1), dtype=np.uint64)
+    _check(_lib().appd_oracle_prim_sym(Wc.ctypes.data, n, dt, mst.ctypes.data, order.ctypes.data),
+           "appd_oracle_prim_sym")
+    return order, mst[: n - 1]
+
+
+def code_ends(codes: np.ndarray, n: int):
+    """(lo, hi) endpoint arrays of edge codes of an n-vertex graph."""
+    c = np.ascontiguousarray(codes, dtype=np.uint64)
+    lo = np.empty(len(c), dtype=np.uint32)
+    hi = np.empty(len(c), dtype=np.uint32)
+    _check(_lib().appd_oracle_code_ends(c.ctypes.data, len(c), n, lo.ctypes.data, hi.ctypes.data),
+           "appd_oracle_code_ends")
+    return lo, hi
+
+
+class short_limit:
+    """Context manager: graphs above ``limit`` vertices use the rank form of
+    the pair number (tests of that form on small graphs)."""
+
+    def __init__(self, limit: int):
+        self.limit = limit
+
+    def __enter__(self):
+        _lib().appd_oracle_set_short_limit(self.limit)
+        return self
+
+    def __exit__(self, *exc):
+        _lib().appd_oracle_set_short_limit(65536)
+        return False
 
 
 def tree_rows(W: np.ndarray, mst: np.ndarray, sources, widest: bool = False) -> np.ndarray:

@@ -90,17 +90,89 @@ static uint32_t w_bits(const uint32_t *W, int64_t n, int64_t i, int64_t j)
     return (i < j) ? W[i * n + j] : W[j * n + i];
 }
 
-/* Edge identity under the strict total order: key, then lo, then hi. */
+/*
+ * Edge identity under the strict total order: key, then lo, then hi.  The
+ * code is key << 32 | p(lo, hi), where the pair number p grows with (lo, hi)
+ * taken lexicographically, so comparing codes compares (key, lo, hi).  Up to
+ * 65536 vertices p = lo << 16 | hi.  Above that (the paper sets no limit on
+ * n; 32 bits of pair number reach ORACLE_MAX_N vertices) p is the pair's
+ * rank among all pairs in that order: the pairs (l, .) with l < lo come first,
+ * n - 1 - l of them for each l, then hi - lo - 1 pairs (lo, .) below hi.
+ */
+#define ORACLE_MAX_N 92682
+/* graphs with at most this many vertices use lo << 16 | hi; tests lower it
+ * to run the rank form on small graphs */
+static int64_t g_short_limit = 65536;
+
+void appd_oracle_set_short_limit(int64_t limit) { g_short_limit = limit < 65536 ? limit : 65536; }
+
+static int64_t pairs_before_row(int64_t l, int64_t n)
+{
+    /* sum over r < l of (n - 1 - r) */
+    return l * (n - 1) - l * (l - 1) / 2;
+}
+
+static uint64_t pair_number(int64_t lo, int64_t hi, int64_t n)
+{
+    if (n <= g_short_limit)
+        return ((uint64_t)lo << 16) | (uint64_t)hi;
+    return (uint64_t)(pairs_before_row(lo, n) + (hi - lo - 1));
+}
+
+static void pair_of_number(uint64_t p, int64_t n, int64_t *lo, int64_t *hi)
+{
+    if (n <= g_short_limit) {
+        *lo = (int64_t)((p >> 16) & 0xFFFF);
+        *hi = (int64_t)(p & 0xFFFF);
+        return;
+    }
+    /* the last row l whose first pair number is <= p, by bisection */
+    int64_t a = 0, b = n - 2;
+    while (a < b) {
+        int64_t mid = (a + b + 1) / 2;
+        if ((uint64_t)pairs_before_row(mid, n) <= p)
+            a = mid;
+        else
+            b = mid - 1;
+    }
+    *lo = a;
+    *hi = (int64_t)(p - (uint64_t)pairs_before_row(a, n)) + a + 1;
+}
+
 static uint64_t edge_code(const uint32_t *W, int64_t n, int dtype, int64_t a, int64_t b)
 {
     int64_t lo = a < b ? a : b, hi = a < b ? b : a;
     uint64_t k = order_key(w_bits(W, n, lo, hi), dtype);
-    return (k << 32) | ((uint64_t)lo << 16) | (uint64_t)hi;
+    return (k << 32) | pair_number(lo, hi, n);
 }
 
-/* lo/hi live in 16 bits each; the oracle supports n <= 65536. */
-static int64_t code_lo(uint64_t c) { return (int64_t)((c >> 16) & 0xFFFF); }
-static int64_t code_hi(uint64_t c) { return (int64_t)(c & 0xFFFF); }
+/* endpoints of a code of an n-vertex graph */
+static int64_t code_lo(uint64_t c, int64_t n)
+{
+    int64_t lo, hi;
+    pair_of_number(c & 0xFFFFFFFFu, n, &lo, &hi);
+    return lo;
+}
+static int64_t code_hi(uint64_t c, int64_t n)
+{
+    int64_t lo, hi;
+    pair_of_number(c & 0xFFFFFFFFu, n, &lo, &hi);
+    return hi;
+}
+
+/* endpoints of the n-1 codes of an n-vertex graph, for the tests */
+int appd_oracle_code_ends(const uint64_t *codes, int64_t m, int64_t n, uint32_t *lo, uint32_t *hi)
+{
+    if (n <= 1 || n > ORACLE_MAX_N)
+        return -1;
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t a, b;
+        pair_of_number(codes[e] & 0xFFFFFFFFu, n, &a, &b);
+        lo[e] = (uint32_t)a;
+        hi[e] = (uint32_t)b;
+    }
+    return 0;
+}
 
 /* ------------------------------------------------------------------ Prim */
 /*
@@ -113,7 +185,7 @@ static int64_t code_hi(uint64_t c) { return (int64_t)(c & 0xFFFF); }
 int appd_oracle_prim(const uint32_t *W, int64_t n, int dtype,
                      uint64_t *mst, uint32_t *order)
 {
-    if (n <= 0 || n > 65536)
+    if (n <= 0 || n > ORACLE_MAX_N)
         return -1;
     uint64_t *dist = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
     unsigned char *in = (unsigned char *)calloc((size_t)n, 1);
@@ -152,6 +224,54 @@ int appd_oracle_prim(const uint32_t *W, int64_t n, int dtype,
     return 0;
 }
 
+/*
+ * The same Prim for a W that is symmetric bit for bit (W(i,j) == W(j,i)),
+ * reading the new vertex's whole row instead of the upper triangle: W(lo,hi)
+ * is then W(best,v) whichever of the two is smaller, and every read is
+ * sequential, so the n = 92682 matrices (34 GB) take minutes instead of a
+ * strided column walk per step.  Same output as appd_oracle_prim on such W.
+ */
+int appd_oracle_prim_sym(const uint32_t *W, int64_t n, int dtype, uint64_t *mst, uint32_t *order)
+{
+    if (n <= 0 || n > ORACLE_MAX_N)
+        return -1;
+    uint64_t *dist = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    unsigned char *in = (unsigned char *)calloc((size_t)n, 1);
+    if (!dist || !in) {
+        free(dist);
+        free(in);
+        return -2;
+    }
+    in[0] = 1;
+    order[0] = 0;
+    for (int64_t v = 1; v < n; ++v)
+        dist[v] = ((uint64_t)order_key(W[v], dtype) << 32) | pair_number(0, v, n);
+    for (int64_t step = 1; step < n; ++step) {
+        int64_t best = -1;
+        for (int64_t v = 0; v < n; ++v) {
+            if (in[v])
+                continue;
+            if (best < 0 || dist[v] < dist[best])
+                best = v;
+        }
+        in[best] = 1;
+        order[step] = (uint32_t)best;
+        mst[step - 1] = dist[best];
+        const uint32_t *row = W + best * n;
+        for (int64_t v = 0; v < n; ++v) {
+            if (in[v])
+                continue;
+            const int64_t lo = v < best ? v : best, hi = v < best ? best : v;
+            const uint64_t c = ((uint64_t)order_key(row[v], dtype) << 32) | pair_number(lo, hi, n);
+            if (c < dist[v])
+                dist[v] = c;
+        }
+    }
+    free(dist);
+    free(in);
+    return 0;
+}
+
 /* ------------------------------------------------------- MST adjacency */
 typedef struct {
     int64_t n;
@@ -172,13 +292,13 @@ static int build_adj(tree_adj *t, int64_t n, const uint64_t *edges, int64_t m)
         return -2;
     }
     for (int64_t e = 0; e < m; ++e) {
-        t->off[code_lo(edges[e]) + 1]++;
-        t->off[code_hi(edges[e]) + 1]++;
+        t->off[code_lo(edges[e], n) + 1]++;
+        t->off[code_hi(edges[e], n) + 1]++;
     }
     for (int64_t v = 0; v < n; ++v)
         t->off[v + 1] += t->off[v];
     for (int64_t e = 0; e < m; ++e) {
-        int64_t a = code_lo(edges[e]), b = code_hi(edges[e]);
+        int64_t a = code_lo(edges[e], n), b = code_hi(edges[e], n);
         int64_t pa = t->off[a] + fill[a]++;
         t->nbr[pa] = b;
         t->eid[pa] = e;
@@ -253,7 +373,7 @@ static int cmp_ci_asc(const void *a, const void *b)
 /* original bits of an MST edge, read back from W */
 static uint32_t edge_bits(const uint32_t *W, int64_t n, uint64_t code)
 {
-    return w_bits(W, n, code_lo(code), code_hi(code));
+    return w_bits(W, n, code_lo(code, n), code_hi(code, n));
 }
 
 /*
@@ -267,7 +387,7 @@ static uint32_t edge_bits(const uint32_t *W, int64_t n, uint64_t code)
 int appd_oracle_alg4(const uint32_t *W, int64_t n, int dtype, uint32_t *M,
                      int64_t *fill_count)
 {
-    if (n < 0 || n > 65536)
+    if (n < 0 || n > ORACLE_MAX_N)
         return -1;
     if (n == 0)
         return 0;
@@ -315,8 +435,8 @@ int appd_oracle_alg4(const uint32_t *W, int64_t n, int dtype, uint32_t *M,
         removed[e] = 1;
         uint32_t bits = edge_bits(W, n, mst[e]);
         int64_t nt = 0;
-        int64_t c1 = traverse(&t, removed, code_lo(mst[e]), tree1, stack, seen, touched, &nt);
-        int64_t c2 = traverse(&t, removed, code_hi(mst[e]), tree2, stack, seen, touched, &nt);
+        int64_t c1 = traverse(&t, removed, code_lo(mst[e], n), tree1, stack, seen, touched, &nt);
+        int64_t c2 = traverse(&t, removed, code_hi(mst[e], n), tree2, stack, seen, touched, &nt);
         for (int64_t a = 0; a < nt; ++a)
             seen[touched[a]] = 0;
         for (int64_t a = 0; a < c1; ++a) {
@@ -352,7 +472,7 @@ int appd_oracle_alg4(const uint32_t *W, int64_t n, int dtype, uint32_t *M,
  */
 int appd_oracle_ascending(const uint32_t *W, int64_t n, int dtype, uint32_t *M)
 {
-    if (n < 0 || n > 65536)
+    if (n < 0 || n > ORACLE_MAX_N)
         return -1;
     for (int64_t i = 0; i < n * n; ++i)
         M[i] = 0;
@@ -378,7 +498,7 @@ int appd_oracle_ascending(const uint32_t *W, int64_t n, int dtype, uint32_t *M)
         next[v] = -1;
     }
     for (int64_t k = 0; k < m; ++k) {
-        int64_t a = code_lo(mst[k]), b = code_hi(mst[k]);
+        int64_t a = code_lo(mst[k], n), b = code_hi(mst[k], n);
         while (parent[a] != a)
             a = parent[a] = parent[parent[a]];
         while (parent[b] != b)
@@ -508,7 +628,7 @@ int appd_oracle_tree_rows(const uint32_t *W, int64_t n, int dtype, const uint64_
                           const uint32_t *src, int64_t nsrc, uint32_t *rows)
 {
     (void)dtype;
-    if (n <= 0 || n > 65536)
+    if (n <= 0 || n > ORACLE_MAX_N)
         return -1;
     int64_t m = n - 1;
     tree_adj t;
@@ -572,7 +692,7 @@ int appd_oracle_prim_rows(const uint32_t *W, int64_t n, int dtype, const uint64_
                           const uint32_t *order, const uint32_t *src, int64_t nsrc, uint32_t *rows)
 {
     (void)dtype;
-    if (n <= 0 || n > 65536)
+    if (n <= 0 || n > ORACLE_MAX_N)
         return -1;
     int64_t *rank = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     if (!rank)
@@ -651,7 +771,7 @@ int appd_oracle_points_w(const float *X, int64_t n, int d, uint32_t *W)
  */
 int appd_oracle_insert(const uint32_t *M, int64_t n, int dtype, const uint32_t *w, uint32_t *Mout)
 {
-    if (n < 0 || n > 65536)
+    if (n < 0 || n > ORACLE_MAX_N)
         return -1;
     uint32_t *d = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n + 1));
     if (!d)

@@ -13,7 +13,8 @@ LIB = os.path.join(OUT_DIR, "libappd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["appd_api.cu", "mst_kernels.cu", "leaf_order.cu", "fill.cu", "server.cu", "batched.cu",
-           "noalloc.cu", "tune.cu", "insert.cu", "contract_tma.cu", "points.cu"]
+           "noalloc.cu", "tune.cu", "insert.cu", "contract_tma.cu", "points.cu",
+           "insert_tree.cu"]
 HEADERS = ["common.cuh", "internal.h", "mst_device.cuh", "leaf_device.cuh", "fill_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

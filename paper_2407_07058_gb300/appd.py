@@ -25,7 +25,8 @@ STATUS = {0: "APPD_OK", 1: "APPD_ERR_INVALID", 2: "APPD_ERR_TOO_LARGE", 3: "APPD
 
 # every symbol that include/appd.h declares
 EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_points", "appd_solve_alg4", "appd_solve_host",
-           "appd_solve_host_async", "appd_solve_host_wait", "appd_solve_noalloc", "appd_insert_vertex", "appd_mst", "appd_leaf_order",
+           "appd_solve_host_async", "appd_solve_host_wait", "appd_solve_noalloc", "appd_insert_vertex", "appd_insert_vertex_tree", "appd_mst",
+           "appd_mst_edges", "appd_leaf_order",
            "appd_solve_batched", "appd_batched_tuning", "appd_batched_autotune",
            "appd_batched_get_tuning", "appd_check_symmetric",
            "appd_last_device_status", "appd_probe_bounded_wait", "appd_release_workspaces",
@@ -64,8 +65,10 @@ def load(build_if_missing: bool = True):
             "appd_solve_host_async": [vp, i64, ci, vp, vp],
             "appd_solve_host_wait": [vp],
             "appd_insert_vertex": [vp, i64, ci, vp, vp, vp],
+            "appd_insert_vertex_tree": [vp, vp, vp, i64, ci, vp, vp, vp, vp, vp, vp],
             "appd_solve_noalloc": [vp, i64, ci, vp, vp],
             "appd_mst": [vp, i64, ci, vp, vp],
+            "appd_mst_edges": [vp, i64, ci, vp, vp, vp, vp],
             "appd_leaf_order": [vp, i64, ci, vp, vp, vp],
             "appd_solve_batched": [vp, vp, vp, vp, vp, i32, vp],
             "appd_batched_tuning": [i32, i32, i64],
@@ -201,6 +204,31 @@ def insert_vertex(M, w, out=None, stream=None, widest: bool = False):
     return Mo
 
 
+def insert_vertex_tree(tree, w, n: int, dtype, out=None, tree_out: bool = True, stream=None,
+                       widest: bool = False):
+    """Warm start through the tree: tree = (keys, lo, hi) of G (mst_edges),
+    w the n weights of the new vertex's edges (CUDA, dtype float32 or int32).
+    Returns (M_out, new tree or None)."""
+    import torch
+    keys, lo, hi = tree
+    if not w.is_cuda or w.numel() != n:
+        raise ValueError("w must be a CUDA vector of n weights")
+    dev = w.device
+    Mo = torch.empty((n + 1, n + 1), dtype=w.dtype, device=dev) if out is None else out
+    nt = None
+    if tree_out:
+        nt = tuple(torch.empty(max(n, 1), dtype=torch.int32, device=dev) for _ in range(3))
+    dt = (F32 if dtype == torch.float32 else U32) | (WIDEST if widest else 0)
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    with torch.cuda.device(dev):
+        _check(load().appd_insert_vertex_tree(ptr(keys), ptr(lo), ptr(hi), n, dt, w.contiguous().data_ptr(),
+                                              Mo.data_ptr(), *(ptr(t) for t in (nt or (None,) * 3)),
+                                              _stream_ptr(stream)), "appd_insert_vertex_tree")
+    if nt is not None:
+        nt = tuple(t[:n] for t in nt)
+    return Mo, nt
+
+
 def solve_host_async_ptr(W_ptr: int, n: int, dt: int, M_ptr: int, stream=None):
     """appd_solve_host_async on raw host pointers: enqueue and return (see
     solve_host_wait before reading M)."""
@@ -223,6 +251,20 @@ def mst(W, stream=None, widest: bool = False):
     with torch.cuda.device(W.device):
         _check(load().appd_mst(W.data_ptr(), n, dt, E.data_ptr(), _stream_ptr(stream)), "appd_mst")
     return E[: n - 1]
+
+
+def mst_edges(W, stream=None, widest: bool = False):
+    """The n-1 MST edges as (keys, lo, hi) int32 tensors (the order key of the
+    edge's weight and its endpoints lo < hi), for any n the library takes."""
+    import torch
+    n = _square_cuda(W)
+    m = max(n - 1, 1)
+    keys, lo, hi = (torch.empty(m, dtype=torch.int32, device=W.device) for _ in range(3))
+    dt = _dtype_code(W) | (WIDEST if widest else 0)
+    with torch.cuda.device(W.device):
+        _check(load().appd_mst_edges(W.data_ptr(), n, dt, keys.data_ptr(), lo.data_ptr(), hi.data_ptr(),
+                                     _stream_ptr(stream)), "appd_mst_edges")
+    return keys[: n - 1], lo[: n - 1], hi[: n - 1]
 
 
 def leaf_order(W, stream=None, widest: bool = False):

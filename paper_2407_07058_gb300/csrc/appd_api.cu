@@ -90,6 +90,7 @@ size_t appd::workspace_layout(Workspace& w, char* base, int64_t cap)
         w.lr_d[i] = (u32*)take(2 * N * sizeof(u32) + 16);
         w.lr_nx[i] = (u32*)take(2 * N * sizeof(u32) + 16);
         w.skey[i] = (u64*)take((N + 1) * 8);
+        w.sval[i] = (u32*)take((N + 1) * sizeof(u32));
     }
     w.ord = (u64*)take(N * 8);
     w.jump = (u32*)take((size_t)lv * N * sizeof(u32));
@@ -108,8 +109,6 @@ cudaError_t appd::workspace_create(int64_t n, Workspace** out)
     int64_t cap = 1024;
     while (cap < n)
         cap *= 2;
-    if (cap > 65536)
-        cap = 65536;
     Workspace* nw = new Workspace();
     nw->device = dev;
     nw->cap = cap;
@@ -213,7 +212,7 @@ appd_status check_args(const void* W, int64_t n, int dt, const void* M)
 {
     if (n < 0 || !W || !M || !dtype_ok(dt))
         return APPD_ERR_INVALID;
-    if (n > 65536)
+    if (n > (int64_t)MAX_N)
         return APPD_ERR_TOO_LARGE;
     if (M != W) {
         const char* a = (const char*)W;
@@ -458,7 +457,7 @@ appd_status appd_solve_points(const float* X, int64_t n, int32_t d, appd_dtype d
 {
     if (n < 0 || !X || !M || (dt != APPD_F32 && dt != APPD_F32_WIDEST) || points_dim(d) == 0)
         return APPD_ERR_INVALID;
-    if (n > 65536)
+    if (n > (int64_t)MAX_N)
         return APPD_ERR_TOO_LARGE;
     {
         const char* a = (const char*)X;
@@ -477,7 +476,9 @@ appd_status appd_solve_points(const float* X, int64_t n, int32_t d, appd_dtype d
         return st;
     Workspace& w = *c.ws;
     const int D = points_dim(d);
-    const size_t need = (size_t)points_rows_padded((u32)n) * D * sizeof(float);
+    // two coordinate arrays (vertex order, component order) and two u32 per row
+    auto bytes_for = [](size_t rows, int dim) { return rows * dim * sizeof(float) * 2 + rows * 8; };
+    const size_t need = bytes_for(points_rows_padded((u32)n), D);
     if (w.pscratch_bytes < need) {
         cudaDeviceSynchronize();
         cudaFree(w.pscratch);
@@ -485,7 +486,7 @@ appd_status appd_solve_points(const float* X, int64_t n, int32_t d, appd_dtype d
         w.pscratch_bytes = 0;
         // sized for the workspace's capacity at 32 dimensions, so that it is
         // allocated once
-        const size_t full = (size_t)points_rows_padded((u32)w.cap) * 32 * sizeof(float);
+        const size_t full = bytes_for(points_rows_padded((u32)w.cap), 32);
         cudaError_t e = cudaMalloc(&w.pscratch, full);
         if (e != cudaSuccess)
             return cuda_fail(e);
@@ -497,7 +498,13 @@ appd_status appd_solve_points(const float* X, int64_t n, int32_t d, appd_dtype d
         return cuda_fail(e);
     set_sizes(w, n);
     g_last_ctr = w.ctr;
-    const PointsSrc ps{w.pscratch, D};
+    const size_t rows = points_rows_padded((u32)n);
+    PointsSrc ps;
+    ps.P = w.pscratch;
+    ps.D = D;
+    ps.Ps = w.pscratch + rows * D;
+    ps.pvid = (u32*)(w.pscratch + 2 * rows * D);
+    ps.pcomp = ps.pvid + rows;
     e = run_mst(w, nullptr, (int)dt, M, contraction_scratch_bytes(n), c.status, cs, &ps);
     if (e == cudaSuccess) {
         prof_begin(PH_LEAF, cs);
@@ -736,7 +743,7 @@ appd_status appd_insert_vertex(const void* M, int64_t n, appd_dtype dt, const vo
 {
     if (n < 0 || (n > 0 && (!M || !w)) || !M_out || !dtype_ok((int)dt))
         return APPD_ERR_INVALID;
-    if (n > 65536)
+    if (n + 1 > (int64_t)MAX_N)
         return APPD_ERR_TOO_LARGE;
     const char* o = (const char*)M_out;
     const size_t ob = (size_t)(n + 1) * (size_t)(n + 1) * 4;
@@ -755,11 +762,67 @@ appd_status appd_insert_vertex(const void* M, int64_t n, appd_dtype dt, const vo
     return e == cudaSuccess ? APPD_OK : cuda_fail(e);
 }
 
+appd_status appd_insert_vertex_tree(const uint32_t* keys, const uint32_t* lo, const uint32_t* hi,
+                                    int64_t n, appd_dtype dt, const void* w, void* M_out,
+                                    uint32_t* keys_out, uint32_t* lo_out, uint32_t* hi_out,
+                                    appd_stream_t s)
+{
+    const bool outs = keys_out || lo_out || hi_out;
+    if (n < 0 || !M_out || !dtype_ok((int)dt) || (n > 0 && !w) || (n > 1 && (!keys || !lo || !hi)) ||
+        (outs && n > 0 && (!keys_out || !lo_out || !hi_out)))
+        return APPD_ERR_INVALID;
+    if (n + 1 > (int64_t)MAX_N)
+        return APPD_ERR_TOO_LARGE;
+    {
+        const char* o = (const char*)M_out;
+        const size_t ob = (size_t)(n + 1) * (size_t)(n + 1) * 4;
+        auto overlaps = [&](const void* p, size_t bytes) {
+            const char* a = (const char*)p;
+            return p && a < o + ob && o < a + bytes;
+        };
+        const size_t eb = (size_t)(n > 0 ? n - 1 : 0) * 4;
+        if (overlaps(w, (size_t)n * 4) || overlaps(keys, eb) || overlaps(lo, eb) || overlaps(hi, eb) ||
+            overlaps(keys_out, (size_t)n * 4) || overlaps(lo_out, (size_t)n * 4) || overlaps(hi_out, (size_t)n * 4))
+            return APPD_ERR_ALIAS;
+    }
+    cudaStream_t cs = (cudaStream_t)s;
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(M_out, 0, 4, cs);
+        return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    SolveCtx c;
+    appd_status st;
+    if ((st = prepare(n + 1, c)) != APPD_OK)
+        return st;
+    Workspace& ws = *c.ws;
+    cudaError_t e = run_insert_tree(ws, keys, lo, hi, (const u32*)w, (u32)n, (int)dt, c.status, cs);
+    set_sizes(ws, n + 1);
+    g_last_ctr = ws.ctr;
+    if (e == cudaSuccess) {
+        prof_begin(PH_LEAF, cs);
+        e = run_leaf_order(ws, c.status, cs);
+        prof_end(PH_LEAF, cs);
+        prof_launches(1);
+    }
+    if (e == cudaSuccess) {
+        prof_begin(PH_FILL, cs);
+        e = run_fill(ws, (int)dt, M_out, cs);
+        prof_end(PH_FILL, cs);
+        prof_launches(1);
+    }
+    if (e == cudaSuccess && outs)
+        e = launch_mst_split(ws.mst, (u32)(n + 1), keys_out, lo_out, hi_out, cs);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
 appd_status appd_mst(const void* W, int64_t n, appd_dtype dt, uint64_t* edges_out, appd_stream_t s)
 {
     appd_status st = check_args(W, n, (int)dt, edges_out);
     if (st == APPD_ERR_ALIAS)
         st = APPD_OK;
+    if (st == APPD_OK && n > (int64_t)SHORT_N)
+        st = APPD_ERR_TOO_LARGE;   // the endpoints of this format have 16 bits
     if (st != APPD_OK || n <= 1)
         return st;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -770,8 +833,31 @@ appd_status appd_mst(const void* W, int64_t n, appd_dtype dt, uint64_t* edges_ou
         return st;
     if ((st = mst_and_order(c, W, n, (int)dt, c.ws->cscratch, false, (cudaStream_t)s)) != APPD_OK)
         return st;
+    // up to SHORT_N vertices the packed edges already are key << 32 | lo << 16 | hi
     cudaError_t e = cudaMemcpyAsync(edges_out, c.ws->mst, (size_t)(n - 1) * 8,
                                     cudaMemcpyDeviceToDevice, (cudaStream_t)s);
+    return e == cudaSuccess ? APPD_OK : cuda_fail(e);
+}
+
+appd_status appd_mst_edges(const void* W, int64_t n, appd_dtype dt, uint32_t* keys, uint32_t* lo,
+                           uint32_t* hi, appd_stream_t s)
+{
+    if (n < 0 || !W || !dtype_ok((int)dt) || (n > 1 && (!keys || !lo || !hi)))
+        return APPD_ERR_INVALID;
+    if (n > (int64_t)MAX_N)
+        return APPD_ERR_TOO_LARGE;
+    if (n <= 1)
+        return APPD_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    SolveCtx c;
+    appd_status st;
+    if ((st = prepare(n, c)) != APPD_OK)
+        return st;
+    if ((st = ensure_cscratch(*c.ws, n)) != APPD_OK)
+        return st;
+    if ((st = mst_and_order(c, W, n, (int)dt, c.ws->cscratch, false, (cudaStream_t)s)) != APPD_OK)
+        return st;
+    cudaError_t e = launch_mst_split(c.ws->mst, (u32)n, keys, lo, hi, (cudaStream_t)s);
     return e == cudaSuccess ? APPD_OK : cuda_fail(e);
 }
 
@@ -780,7 +866,7 @@ appd_status appd_leaf_order(const void* W, int64_t n, appd_dtype dt, uint32_t* p
 {
     if (n < 0 || !W || !pos_out || (n > 1 && !gap_out) || !dtype_ok((int)dt))
         return APPD_ERR_INVALID;
-    if (n > 65536)
+    if (n > (int64_t)MAX_N)
         return APPD_ERR_TOO_LARGE;
     if (n == 0)
         return APPD_OK;
@@ -812,7 +898,7 @@ appd_status appd_solve_batched(const int64_t* offsets, const void* Ws, const int
     for (int32_t g = 0; g < count; ++g) {
         if (ns[g] < 0 || offsets[g] < 0)
             return APPD_ERR_INVALID;
-        if (ns[g] > 65536)
+        if (ns[g] > (int64_t)MAX_N)
             return APPD_ERR_TOO_LARGE;
         if (dts && !dtype_ok(dts[g]))
             return APPD_ERR_INVALID;
@@ -890,7 +976,7 @@ appd_status appd_check_symmetric(const void* W, int64_t n, appd_dtype dt, appd_s
 {
     if (n < 0 || !W || !dtype_ok((int)dt))
         return APPD_ERR_INVALID;
-    if (n > 65536)
+    if (n > (int64_t)MAX_N)
         return APPD_ERR_TOO_LARGE;
     if (n <= 1)
         return APPD_OK;

@@ -37,6 +37,7 @@ struct SliceWs {
     u64* mxo;
     u32* nha;
     u64 *skey0, *skey1;
+    u32 *sval0, *sval1;
     u32 *hist, *first_child, *next_sib, *pos, *order, *nsize, *gap, *st;
     u64* cscratch;   // contraction matrices for in-place graphs (M == W), or null
 };
@@ -59,9 +60,12 @@ struct BatchArgs {
     u64* best0;           // round-1 minima of all graphs (k_rowmin_batched)
     const u64* row_off;   // graph g's minima at best0 + row_off[g]
     u32* gfail;           // per graph: 1 when its solve failed (the fill skips it)
+    u32 prim_max;         // graphs up to this size are solved by one warp with Prim
 };
 
 constexpr int BATCH_THREADS = 512;
+// largest graph a warp solves by Prim (a lane keeps n / 32 distances)
+constexpr u32 PRIM_WARP_MAX = 512;
 
 // Column groups of a row that starts at any 4-byte boundary.
 //
@@ -183,7 +187,7 @@ __device__ void row_best_warp(const u32* __restrict__ W, u32 n, u32 i, u64* __re
     const u32 kmin = __reduce_min_sync(0xFFFFFFFFu, bj == 0xFFFFFFFFu ? 0xFFFFFFFFu : bk);
     const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, (bj != 0xFFFFFFFFu && bk == kmin) ? bj : 0xFFFFFFFFu);
     if (lane == 0)
-        best[i] = pack_edge(kmin, i, jmin);
+        best[i] = pack_edge(kmin, i, jmin, n);
 }
 
 // Round-1 minima of every graph of a batch before k_batched: one CTA per
@@ -299,7 +303,7 @@ __device__ void contract_level_warps(const ContractArgs& a, u32 cr, u32 cn, u32 
                                 lab.w = A;
                         }
                         const uint4 x[4] = {v[0][u], v[1][u], v[2][u], v[3][u]};
-                        fold_group<DT, 4, true>(x, rid, 4 * g, lab, A, 0, cn, bins);
+                        fold_group<DT, 4, true>(x, rid, 4 * g, lab, A, 0, cn, bins, cr);
                     }
                 }
             } else {
@@ -516,6 +520,8 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, u32* po
     la.nha = w.nha;
     la.skey0 = w.skey0;
     la.skey1 = w.skey1;
+    la.sval0 = w.sval0;
+    la.sval1 = w.sval1;
     la.hist = w.hist;
     la.ntiles = (n - 1 + 2047) / 2048;
     la.first_child = w.first_child;
@@ -538,6 +544,122 @@ __device__ void solve_one(const SliceWs& w, const u32* W, u32* M, u32 n, u32* po
     __syncthreads();
 }
 
+// A small graph on one warp, by Prim's algorithm from vertex 0 (Section 3's
+// MST step, as the paper does it): each lane keeps the packed distance of
+// its vertices v = lane + 32 t to the tree, the warp takes the smallest
+// (the strict order (key, lo, hi), so the tree is the minimum spanning tree
+// the other paths find), records the vertex's position and the edge that
+// added it, and relaxes with the new vertex's row.  Prim's visiting order is
+// a leaf order for the fill: M(v_a, v_b) is the largest of the edges that
+// added v_{a+1} .. v_b (the tree path argument of the leaf order), so the
+// positions and the sparse table over those gaps go to the arena exactly as
+// the one-CTA leaf order leaves them, and the grid-wide fill follows.
+template <int DT>
+__device__ void prim_warp(const u32* __restrict__ W, u32* M, u32 n, u32* pos, u32* fail_g)
+{
+    constexpr int T = PRIM_WARP_MAX / 32;
+    const u32 lane = threadIdx.x & 31;
+    if (n == 1) {
+        if (lane == 0) {
+            M[0] = 0u;
+            pos[0] = 0u;
+            *fail_g = 0u;
+        }
+        __syncwarp();
+        return;
+    }
+    u32* st = pos + n;
+    u64 dist[T];
+    u32 out = 0;   // bit t: vertex lane + 32 t is in the tree (or past n)
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const u32 v = lane + 32 * t;
+        dist[t] = EDGE_INF;
+        if (v >= n || v == 0)
+            out |= 1u << t;
+        else
+            dist[t] = pack_edge(key_of(W[v], DT), 0, v, n);
+    }
+    if (lane == 0)
+        pos[0] = 0u;
+    for (u32 k = 1; k < n; ++k) {
+        u64 m = EDGE_INF;
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            if (!((out >> t) & 1u) && dist[t] < m)
+                m = dist[t];
+        const u64 e = warp_min_u64(m);
+        // the unique slot that holds e: the vertex that joins
+        u32 b = 0xFFFFFFFFu;
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            if (!((out >> t) & 1u) && dist[t] == e) {
+                b = lane + 32 * t;
+                out |= 1u << t;
+            }
+        b = __reduce_min_sync(0xFFFFFFFFu, b);
+        if (lane == 0) {
+            pos[b] = k;
+            st[k - 1] = edge_key(e);
+        }
+        const u32* row = W + (size_t)b * n;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const u32 v = lane + 32 * t;
+            if (!((out >> t) & 1u)) {
+                const u64 c = pack_edge(key_of(row[v], DT), b, v, n);
+                dist[t] = c < dist[t] ? c : dist[t];
+            }
+        }
+    }
+    __syncwarp();
+    // the sparse table over the n - 1 gaps, one level at a time
+    const u32 m = n - 1;
+    for (u32 k = 1; (1u << k) <= m; ++k) {
+        const u32 h = 1u << (k - 1);
+        const u32* sp = st + (size_t)(k - 1) * n;
+        u32* sc = st + (size_t)k * n;
+        for (u32 x = lane; x + 2 * h <= m; x += 32) {
+            const u32 p = sp[x], q = sp[x + h];
+            sc[x] = p > q ? p : q;
+        }
+        __syncwarp();
+    }
+    if (lane == 0)
+        *fail_g = 0u;
+    __syncwarp();
+}
+
+template <int DT>
+__device__ __forceinline__ void prim_graph(const BatchArgs& b, u32 g)
+{
+    prim_warp<DT>(b.wp[g], b.mp[g], b.ns[g], b.posst + b.pst_off[g], b.gfail + g);
+}
+
+// Graphs of at most prim_max vertices, one per warp, claimed warp by warp.
+__device__ void prim_warps(const BatchArgs& b, u32 first_q)
+{
+    const u32 lane = threadIdx.x & 31;
+    u32 q = first_q;
+    for (;;) {
+        if (q >= b.count)
+            break;
+        const u32 g = b.queue[q];
+        if (b.ns[g] > 0) {
+            switch (b.dts[g]) {
+            case 1: prim_graph<1>(b, g); break;
+            case 2: prim_graph<2>(b, g); break;
+            case 3: prim_graph<3>(b, g); break;
+            default: prim_graph<0>(b, g); break;
+            }
+        }
+        u32 nq = 0;
+        if (lane == 0)
+            nq = atomicAdd(b.next, 1u);
+        q = __shfl_sync(0xFFFFFFFFu, nq, 0);
+    }
+}
+
 __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -557,6 +679,19 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched(BatchArgs b)
         const u32 n = b.ns[g];
         const u32* W = b.wp[g];
         u32* M = b.mp[g];
+        if (n <= b.prim_max) {
+            // the queue is sorted by size: every graph from here on is small;
+            // warp 0 takes this one, the other warps claim their own
+            u32 q0 = q;
+            if ((threadIdx.x >> 5) != 0) {
+                u32 nq = 0;
+                if ((threadIdx.x & 31) == 0)
+                    nq = atomicAdd(b.next, 1u);
+                q0 = __shfl_sync(0xFFFFFFFFu, nq, 0);
+            }
+            prim_warps(b, q0);
+            break;
+        }
         if (n == 0)
             continue;
         u32* pos_g = b.posst + b.pst_off[g];
@@ -661,6 +796,8 @@ SliceWs to_slice(const Workspace& w)
     s.nha = w.nha;
     s.skey0 = w.skey[0];
     s.skey1 = w.skey[1];
+    s.sval0 = w.sval[0];
+    s.sval1 = w.sval[1];
     s.hist = w.hist;
     s.first_child = w.first_child;
     s.next_sib = w.next_sib;
@@ -711,7 +848,7 @@ inline u32 st_levels_of(u32 n)
     return l;
 }
 
-DescLayout desc_layout(const BatchDesc& d, u32 fill_rows)
+DescLayout desc_layout(const BatchDesc& d, u32 fill_rows, u32 prim_max)
 {
     DescLayout L;
     const size_t cnt = d.n.size();
@@ -720,7 +857,8 @@ DescLayout desc_layout(const BatchDesc& d, u32 fill_rows)
     for (u32 n : d.n) {
         if (n >= 2) {
             L.ntiles += (n + FC - 1) / FC;
-            L.ntasks += (n + ROWB_ROWS - 1) / ROWB_ROWS;
+            if (n > prim_max)   // round-1 minima only for the graphs Boruvka solves
+                L.ntasks += (n + ROWB_ROWS - 1) / ROWB_ROWS;
         }
         L.posst_words += (size_t)n * (1 + st_levels_of(n));
         L.rows += n;
@@ -741,7 +879,8 @@ DescLayout desc_layout(const BatchDesc& d, u32 fill_rows)
     return L;
 }
 
-void fill_desc(const BatchDesc& d, u32 fill_rows, const DescLayout& L, std::vector<unsigned char>& host)
+void fill_desc(const BatchDesc& d, u32 fill_rows, u32 prim_max, const DescLayout& L,
+               std::vector<unsigned char>& host)
 {
     const u32 cnt = (u32)d.n.size();
     std::vector<u32> q(cnt);
@@ -760,8 +899,9 @@ void fill_desc(const BatchDesc& d, u32 fill_rows, const DescLayout& L, std::vect
         const u32 n = d.n[g];
         if (n < 2)
             continue;
-        for (u32 r0 = 0; r0 < n; r0 += ROWB_ROWS)
-            tasks.push_back(make_uint2(g, r0));
+        if (n > prim_max)
+            for (u32 r0 = 0; r0 < n; r0 += ROWB_ROWS)
+                tasks.push_back(make_uint2(g, r0));
         // a tile is a whole column block: its sort and table are built once,
         // the rows follow in batches of fill_rows
         for (u32 j0 = 0; j0 < n; j0 += FC)
@@ -805,6 +945,7 @@ BatchArgs make_args(const BatchRuntime& rt, void* dev, const DescLayout& L, u32 
     a.bin_cap = rt.bin_cap;
     a.warp_bins = rt.warp_bins;
     a.fill_rows = (u32)rt.tune.fill_rows;
+    a.prim_max = rt.tune.prim_max < PRIM_WARP_MAX ? rt.tune.prim_max : PRIM_WARP_MAX;
     return a;
 }
 
@@ -931,7 +1072,8 @@ cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cuda
     if (inplace && (e = ensure_scratch(rt)) != cudaSuccess)
         return e;
     const u32 fr = (u32)rt.tune.fill_rows;
-    const DescLayout L = desc_layout(d, fr);
+    const u32 pm = rt.tune.prim_max < PRIM_WARP_MAX ? rt.tune.prim_max : PRIM_WARP_MAX;
+    const DescLayout L = desc_layout(d, fr, pm);
     std::vector<unsigned char> host(L.bytes);
     if (!cache_graph) {
         // one descriptor block and one arena per runtime: launches on the
@@ -964,7 +1106,7 @@ cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cuda
                 return e;
             rt.arena_bytes = b;
         }
-        fill_desc(d, fr, L, host);
+        fill_desc(d, fr, pm, L, host);
         // pageable source: the copy is staged before the call returns
         if ((e = cudaMemcpyAsync(rt.d_desc, host.data(), L.bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return e;
@@ -997,7 +1139,7 @@ cudaError_t batch_launch(BatchRuntime& rt, const BatchDesc& d, u32* status, cuda
             drop();
             return e;
         }
-        fill_desc(d, fr, L, host);
+        fill_desc(d, fr, pm, L, host);
         if ((e = cudaMemcpy(p.dev, host.data(), L.bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
             drop();
             return e;

@@ -5,9 +5,13 @@
 // (non-negative: bits | 0x80000000, negative: ~bits).  The transform is a
 // bijection, so outputs are recovered bit-exactly from keys.
 //
-// Packed edges: key << 32 | lo << 16 | hi (lo < hi, both < 65536).  Unsigned
-// comparison of packed edges is a strict total order that refines the weight
-// order, which makes the MST unique and Boruvka's hooking cycle-free.
+// Packed edges: key << 32 | pair(lo, hi), lo < hi.  The 32-bit pair code is
+// increasing in (lo, hi) taken lexicographically, so unsigned comparison of
+// packed edges is the strict total order (key, lo, hi): it refines the weight
+// order, which makes the MST unique and Boruvka's hooking cycle-free.  For
+// n <= 65536 the code is lo << 16 | hi; above that it is the pair's index in
+// the row-major upper triangle, lo * n - lo (lo + 1) / 2 + hi - lo - 1, which
+// fits 32 bits while n (n - 1) / 2 <= 2^32, i.e. n <= MAX_N.
 #pragma once
 
 #include <cstdint>
@@ -46,15 +50,66 @@ __host__ __device__ __forceinline__ u32 bits_of(u32 key, int dt)
 // a valid dtype code (APPD_F32, APPD_U32, either with the widest flag)
 __host__ __device__ __forceinline__ bool dtype_ok(int dt) { return dt >= 0 && dt <= 3; }
 
-__host__ __device__ __forceinline__ u64 pack_edge(u32 key, u32 a, u32 b)
+// the largest n the packed edges support
+constexpr u32 MAX_N = 92682;
+// up to this n the pair code is lo << 16 | hi
+constexpr u32 SHORT_N = 65536;
+
+// tri index of (lo, hi) minus hi: lo * n - lo (lo + 1) / 2 - lo - 1, evaluated
+// modulo 2^32 (the true value of the full index lies in [0, 2^32), so the
+// wrapped terms cancel); lo (lo + 1) / 2 is formed without losing the bit a
+// 32-bit product of lo and lo + 1 would drop
+__host__ __device__ __forceinline__ u32 tri_row_base(u32 lo, u32 n)
 {
-    u32 lo = a < b ? a : b, hi = a < b ? b : a;
-    return ((u64)key << 32) | ((u64)lo << 16) | (u64)hi;
+    const u32 half = (lo & 1u) ? lo * ((lo + 1u) >> 1) : (lo >> 1) * (lo + 1u);
+    return lo * n - half - lo - 1u;
+}
+
+// 32-bit code of the pair lo < hi of an n-vertex graph
+__host__ __device__ __forceinline__ u32 pair_code(u32 lo, u32 hi, u32 n)
+{
+    return n <= SHORT_N ? ((lo << 16) | hi) : tri_row_base(lo, n) + hi;
+}
+
+__host__ __device__ __forceinline__ u64 pack_edge(u32 key, u32 a, u32 b, u32 n)
+{
+    const u32 lo = a < b ? a : b, hi = a < b ? b : a;
+    return ((u64)key << 32) | pair_code(lo, hi, n);
+}
+
+// (lo, hi) from a pair code.  For the triangular code, lo is the largest l
+// whose first pair l * n - l (l + 1) / 2 does not exceed the code: a root of
+// that quadratic in double precision, corrected by at most a step or two.
+__host__ __device__ __forceinline__ void pair_decode(u32 t, u32 n, u32* lo, u32* hi)
+{
+    if (n <= SHORT_N) {
+        *lo = t >> 16;
+        *hi = t & 0xFFFFu;
+        return;
+    }
+    const double b = 2.0 * (double)n - 1.0;
+    double disc = b * b - 8.0 * (double)t;
+    if (disc < 0.0)
+        disc = 0.0;
+    long long l = (long long)((b - sqrt(disc)) * 0.5);
+    if (l < 0)
+        l = 0;
+    if (l > (long long)n - 2)
+        l = (long long)n - 2;
+    auto first = [n](long long x) -> u64 { return (u64)x * n - (u64)x * (u64)(x + 1) / 2; };
+    while (l > 0 && first(l) > t)
+        --l;
+    while (l + 1 <= (long long)n - 2 && first(l + 1) <= t)
+        ++l;
+    *lo = (u32)l;
+    *hi = (u32)((u64)t - first(l) + (u64)l + 1);
 }
 
 __host__ __device__ __forceinline__ u32 edge_key(u64 e) { return (u32)(e >> 32); }
-__host__ __device__ __forceinline__ u32 edge_lo(u64 e) { return (u32)(e >> 16) & 0xFFFFu; }
-__host__ __device__ __forceinline__ u32 edge_hi(u64 e) { return (u32)e & 0xFFFFu; }
+__host__ __device__ __forceinline__ void edge_ends(u64 e, u32 n, u32* lo, u32* hi)
+{
+    pair_decode((u32)e, n, lo, hi);
+}
 
 __device__ __forceinline__ int ceil_log2_dev(u32 x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
 

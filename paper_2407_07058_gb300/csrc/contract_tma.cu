@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int c = 0; c < 4; ++c) {
                     rel[c] = L[c] - b0;
                     okc[c] = (L[c] != A) && (rel[c] < nb) && ((u32)c >= cmin);
-                    e[c] = ((u64)bk[4 * t + c] << 32) | ((bi[4 * t + c] << 16) | (j + (u32)c));
+                    e[c] = ((u64)bk[4 * t + c] << 32) | pair_code(bi[4 * t + c], j + (u32)c, cr);
                 }
                 u64 cur[4];
 #pragma unroll

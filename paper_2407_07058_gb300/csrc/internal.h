@@ -11,7 +11,7 @@
 
 namespace appd {
 
-constexpr int MAX_LEVELS = 20;     // Boruvka levels: ceil(log2 65536) = 16, plus slack
+constexpr int MAX_LEVELS = 20;     // Boruvka levels: ceil(log2 MAX_N) = 17, plus slack
 constexpr int CONTRACT_ROWS = 16;  // rows of the current matrix per contraction work item
 constexpr int CONTRACT_THREADS = 1024;   // one contraction CTA per SM
 constexpr int CONTRACT_THREADS2 = 512;   // two per SM (half the bins each)
@@ -66,6 +66,7 @@ struct Workspace {
     u64* mxo = nullptr;
     u32* nha = nullptr;
     u64* skey[2] = {nullptr, nullptr};
+    u32* sval[2] = {nullptr, nullptr};
     u32* hist = nullptr;
     u32 ntiles = 0;
     u32 *first_child = nullptr, *next_sib = nullptr;
@@ -87,8 +88,11 @@ struct Workspace {
 // A point set in place of W (points.cu): P holds n_pad x D zero-padded FP32
 // coordinates; the edge weights are computed where they are used.
 struct PointsSrc {
-    const float* P;
+    const float* P;   // n_pad x D, in vertex order
     int D;
+    float* Ps;        // n_pad x D, the same coordinates in component order (level 0)
+    u32* pvid;        // vertex at each position of that order
+    u32* pcomp;       // its level-0 component
 };
 // padded dimension (2, 4, 8, 16 or 32) of a d-dimensional set, 0 if d is out of range
 int points_dim(int d);
@@ -100,6 +104,12 @@ struct ContractArgs;
 cudaError_t launch_contract_pts(const ContractArgs& ca, const float* P, int D, int dt, int blocks,
                                 cudaStream_t s);
 cudaError_t launch_mst_sqrt(u64* mst, u32 m, int dt, cudaStream_t s);
+cudaError_t launch_pts_gather(const float* P, int D, const u32* members, const u32* label, u32 n, float* Ps,
+                              u32* pvid, u32* pcomp, cudaStream_t s);
+cudaError_t launch_contract_pts_sorted(const ContractArgs& ca, const float* Ps, const u32* pvid,
+                                       const u32* pcomp, int D, int dt, int blocks, cudaStream_t s);
+// the n - 1 packed tree edges as three arrays: key, lo, hi
+cudaError_t launch_mst_split(const u64* mst, u32 n, u32* keys, u32* lo, u32* hi, cudaStream_t s);
 cudaError_t preload_points();
 
 // launch sequence pieces (all asynchronous on the stream); with ps, the
@@ -113,6 +123,12 @@ cudaError_t run_fill_alg4(Workspace& ws, int dt, void* M, u32* status, cudaStrea
 cudaError_t run_insert(const void* M, int64_t n, int dt, const void* w, void* Mo, u32* d, int sms,
                        cudaStream_t s);
 cudaError_t run_fill_trivial(int64_t n, void* M, cudaStream_t s);   // n == 1
+// warm start by a tree update (insert_tree.cu): the minimum spanning tree of
+// G + p from G's tree (n - 1 edges) and p's n weights, into ws.mst (packed
+// for n + 1 vertices)
+cudaError_t run_insert_tree(Workspace& ws, const u32* keys, const u32* lo, const u32* hi, const u32* w,
+                            u32 n, int dt, u32* status, cudaStream_t s);
+cudaError_t preload_insert_tree();
 // level-0 contraction over the upper triangle fed by bulk copies
 // (contract_tma.cu); runs when |C_1| <= run_max, needs n % 4 == 0, W 16-byte
 // aligned, ca.label16 8-byte aligned (n + 8 entries, written by the level-0
@@ -138,9 +154,11 @@ struct BatchTuning {
     int ctas_per_sm = 1;     // persistent CTAs per SM (one workspace slice each)
     int fill_rows = 256;     // rows per fill tile inside a CTA
     int64_t n_split = 2048;  // larger graphs use the single-solve pipeline
+    u32 prim_max = 256;      // graphs up to this size: one warp each, by Prim (<= 512)
     bool operator==(const BatchTuning& o) const
     {
-        return ctas_per_sm == o.ctas_per_sm && fill_rows == o.fill_rows && n_split == o.n_split;
+        return ctas_per_sm == o.ctas_per_sm && fill_rows == o.fill_rows && n_split == o.n_split &&
+               prim_max == o.prim_max;
     }
 };
 // the batched path's current parameters (appd_batched_tuning)

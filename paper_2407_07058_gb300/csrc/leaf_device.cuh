@@ -19,6 +19,7 @@ struct LeafArgs {
     u64* mxo;
     u32* nha;
     u64 *skey0, *skey1;
+    u32 *sval0, *sval1;   // the child vertex carried beside each sort key
     u32* hist;
     u32 ntiles;
     u32 *first_child, *next_sib;
@@ -90,9 +91,10 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
     if (!t.sync())
         return;
     for (u32 e = me; e < m; e += ts) {
-        u64 x = a.mst[e];
-        atomicAdd(&a.deg[edge_lo(x)], 1u);
-        atomicAdd(&a.deg[edge_hi(x)], 1u);
+        u32 lo, hi;
+        edge_ends(a.mst[e], n, &lo, &hi);
+        atomicAdd(&a.deg[lo], 1u);
+        atomicAdd(&a.deg[hi], 1u);
     }
     if (!t.sync())
         return;
@@ -102,8 +104,8 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
     if (!t.sync())
         return;
     for (u32 e = me; e < m; e += ts) {
-        u64 x = a.mst[e];
-        u32 lo = edge_lo(x), hi = edge_hi(x);
+        u32 lo, hi;
+        edge_ends(a.mst[e], n, &lo, &hi);
         u32 s0 = atomicAdd(&a.afill[lo], 1u);
         a.adj[a.adj_off[lo] + s0] = 2 * e;       // arc lo -> hi
         a.aslot[2 * e] = s0;
@@ -116,8 +118,9 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
     // ---- Euler tour successor of every arc; the tour starts at vertex 0
     const u32 first = a.adj[a.adj_off[0]];
     for (u32 x = me; x < na; x += ts) {
-        u64 e = a.mst[x >> 1];
-        u32 dst = (x & 1) ? edge_lo(e) : edge_hi(e);
+        u32 elo, ehi;
+        edge_ends(a.mst[x >> 1], n, &elo, &ehi);
+        u32 dst = (x & 1) ? elo : ehi;
         u32 sl = a.aslot[x ^ 1u] + 1;
         if (sl == a.deg[dst])
             sl = 0;
@@ -138,12 +141,14 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
     // ---- orientation: the earlier arc of an edge goes down the tree
     for (u32 e = me; e < m; e += ts) {
         u64 x = a.mst[e];
-        u32 lo = edge_lo(x), hi = edge_hi(x), key = edge_key(x);
+        u32 lo, hi;
+        edge_ends(x, n, &lo, &hi);
+        const u32 key = edge_key(x);
         bool down_lo_hi = dist[2 * e] > dist[2 * e + 1];   // more arcs after it == earlier
         u32 child = down_lo_hi ? hi : lo, par = down_lo_hi ? lo : hi;
         a.parent[child] = par;
         a.pe_key[child] = key;
-        a.ord[child] = ((u64)key << 16) | child;
+        a.ord[child] = ((u64)key << 32) | child;
     }
     if (me == 0) {
         a.parent[0] = 0;
@@ -160,21 +165,31 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
     }
     if (!t.sync())
         return;
-    for (int k = 1; k < a.levels; ++k) {
+    // two levels per phase from the last complete one: level k is jump^2 of
+    // level k-1 and level k+1 its jump^4, with the maxima over the same hops
+    for (int k = 1; k < a.levels; k += 2) {
         const u32* jp = a.jump + (size_t)(k - 1) * n;
         const u64* mp = a.mxo + (size_t)(k - 1) * n;
         u32* jc = a.jump + (size_t)k * n;
         u64* mc = a.mxo + (size_t)k * n;
+        const bool two = k + 1 < a.levels;
         for (u32 v = me; v < n; v += ts) {
-            u32 j = jp[v];
-            jc[v] = jp[j];
-            u64 x = mp[v], y = mp[j];
-            mc[v] = x > y ? x : y;
+            const u32 j1 = jp[v], j2 = jp[j1];
+            const u64 m01 = mp[v] > mp[j1] ? mp[v] : mp[j1];
+            jc[v] = j2;
+            mc[v] = m01;
+            if (two) {
+                const u32 j3 = jp[j2];
+                const u64 m23 = mp[j2] > mp[j3] ? mp[j2] : mp[j3];
+                jc[(size_t)n + v] = jp[j3];
+                mc[(size_t)n + v] = m01 > m23 ? m01 : m23;
+            }
         }
         if (!t.sync())
             return;
     }
-    // ---- nearest heavier ancestor, and the sort keys (nha, ord)
+    // ---- nearest heavier ancestor, and the sort keys (nha, key of y's
+    // parent edge) with y carried beside them
     for (u32 y = me + 1; y < n; y += ts) {
         u32 z = a.parent[y];
         const u64 tg = a.ord[y];
@@ -183,19 +198,24 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
                 z = a.jump[(size_t)k * n + z];
         }
         a.nha[y] = z;
-        a.skey0[y - 1] = ((u64)z << 48) | tg;
+        a.skey0[y - 1] = ((u64)z << 32) | a.pe_key[y];
+        a.sval0[y - 1] = y;
     }
     if (!t.sync())
         return;
-    // ---- stable LSD radix sort of the keys on bits 16..63 (the input is in
-    // increasing y, which is the lowest field)
+    // ---- stable LSD radix sort of the keys, 8 bits per pass over the key
+    // and the bits that nha needs; the input is in increasing y, so equal
+    // keys keep y ascending and the order is (nha, ord)
+    const int passes = (32 + ceil_log2_dev(n) + 7) / 8;
     {
         u64* in = a.skey0;
         u64* out = a.skey1;
+        u32* vin = a.sval0;
+        u32* vout = a.sval1;
         const u32 ntiles = a.ntiles;
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        for (int pass = 0; pass < 6; ++pass) {
-            const int shift = 16 + 8 * pass;
+        for (int pass = 0; pass < passes; ++pass) {
+            const int shift = 8 * pass;
             for (u32 tile = t.block(); tile < ntiles; tile += t.nblocks()) {
                 for (u32 d = threadIdx.x; d < 256; d += blockDim.x)
                     s_cnt[d] = 0;
@@ -225,6 +245,7 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
                     const u32 i = base + threadIdx.x;
                     const bool valid = i < b1;
                     const u64 key = valid ? in[i] : 0ull;
+                    const u32 val = valid ? vin[i] : 0u;
                     const u32 d = valid ? ((u32)(key >> shift) & 255u) : (256u + lane);
                     const u32 peers = __match_any_sync(0xFFFFFFFFu, d);
                     const u32 rank_w = __popc(peers & ((1u << lane) - 1u));
@@ -244,8 +265,11 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
                         s_cnt[dd] = run;
                     }
                     __syncthreads();
-                    if (valid)
-                        out[s_off[d] + s_wc[w][d] + rank_w] = key;
+                    if (valid) {
+                        const u32 dst = s_off[d] + s_wc[w][d] + rank_w;
+                        out[dst] = key;
+                        vout[dst] = val;
+                    }
                     __syncthreads();
                 }
             }
@@ -254,18 +278,20 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
             u64* tmp = in;
             in = out;
             out = tmp;
+            u32* vt = vin;
+            vin = vout;
+            vout = vt;
         }
-        // 6 passes: the sorted keys are back in skey0
     }
+    // the sorted keys are in skey0 after an even number of passes
+    const u64* sk = (passes & 1) ? a.skey1 : a.skey0;
+    const u32* sv = (passes & 1) ? a.sval1 : a.sval0;
     // ---- first child / next sibling of the nearest-heavier-ancestor tree
     for (u32 i = me; i < m; i += ts) {
-        u64 s = a.skey0[i];
-        u32 p = (u32)(s >> 48), y = (u32)s & 0xFFFFu;
-        if (i == 0 || (u32)(a.skey0[i - 1] >> 48) != p)
+        const u32 p = (u32)(sk[i] >> 32), y = sv[i];
+        if (i == 0 || (u32)(sk[i - 1] >> 32) != p)
             a.first_child[p] = y;
-        a.next_sib[y] = (i + 1 < m && (u32)(a.skey0[i + 1] >> 48) == p)
-                            ? ((u32)a.skey0[i + 1] & 0xFFFFu)
-                            : NONE32;
+        a.next_sib[y] = (i + 1 < m && (u32)(sk[i + 1] >> 32) == p) ? sv[i + 1] : NONE32;
     }
     if (!t.sync())
         return;
@@ -321,13 +347,22 @@ __device__ void leaf_body(const Team& t, const LeafArgs& a)
         a.st[x] = a.gap[x];
     if (!t.sync())
         return;
-    for (int k = 1; k < a.st_levels; ++k) {
+    // two levels per phase from the last complete one (level k - 1):
+    // level k from two of its entries, level k + 1 from four
+    for (int k = 1; k < a.st_levels; k += 2) {
         const u32* sp = a.st + (size_t)(k - 1) * n;
         u32* sc = a.st + (size_t)k * n;
-        const u32 half = 1u << (k - 1);
-        for (u32 x = me; x + 2 * half <= m; x += ts) {
-            u32 p = sp[x], q = sp[x + half];
-            sc[x] = p > q ? p : q;
+        const u32 h = 1u << (k - 1);
+        const bool two = k + 1 < a.st_levels;
+        for (u32 x = me; x + 2 * h <= m; x += ts) {
+            const u32 p = sp[x], q = sp[x + h];
+            const u32 m01 = p > q ? p : q;
+            sc[x] = m01;
+            if (two && x + 4 * h <= m) {
+                const u32 r = sp[x + 2 * h], s = sp[x + 3 * h];
+                const u32 m23 = r > s ? r : s;
+                sc[(size_t)n + x] = m01 > m23 ? m01 : m23;
+            }
         }
         if (!t.sync())
             return;

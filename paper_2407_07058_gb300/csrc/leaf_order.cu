@@ -70,6 +70,8 @@ cudaError_t run_leaf_order(Workspace& ws, u32* status, cudaStream_t s)
     a.nha = ws.nha;
     a.skey0 = ws.skey[0];
     a.skey1 = ws.skey[1];
+    a.sval0 = ws.sval[0];
+    a.sval1 = ws.sval[1];
     a.hist = ws.hist;
     a.ntiles = ws.ntiles;
     a.first_child = ws.first_child;

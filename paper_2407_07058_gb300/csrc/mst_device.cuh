@@ -40,9 +40,11 @@ __device__ void step_body(const Team& t, const StepArgs& a)
     // hook: the other end of each component's best edge
     for (u32 x = me; x < c; x += ts) {
         u64 e = a.best_in[x];
-        u32 h = x;
-        if (e != EDGE_INF && edge_lo(e) < a.n && edge_hi(e) < a.n) {
-            u32 ca = a.comp[edge_lo(e)], cb = a.comp[edge_hi(e)];
+        u32 h = x, lo = 0, hi = 0;
+        if (e != EDGE_INF)
+            edge_ends(e, a.n, &lo, &hi);
+        if (e != EDGE_INF && lo < a.n && hi < a.n) {
+            u32 ca = a.comp[lo], cb = a.comp[hi];
             if (ca != x && cb != x)
                 record_failure(a.status, &ctr->bar.failed, DEV_INTERNAL);
             h = (ca == x) ? cb : ca;
@@ -195,7 +197,7 @@ __device__ __forceinline__ u32 lane_of_dyn(const uint4& v, int c)
 // wins, rows ascending), packed with its endpoints, folded into bin L
 template <int DT, int NR, int C>
 __device__ __forceinline__ void column_w(const uint4* v, const u32* rid, u32 j, u32 L, u32 A, u32 b0,
-                                         u32 nb, u64* bins)
+                                         u32 nb, u64* bins, u32 n)
 {
     const u32 rel = L - b0;
     if (L == A || rel >= nb)
@@ -209,7 +211,7 @@ __device__ __forceinline__ void column_w(const uint4* v, const u32* rid, u32 j, 
             bi = rid[q];
         }
     }
-    const u64 e = pack_edge(bk, bi, j);
+    const u64 e = pack_edge(bk, bi, j, n);
     u64* slot = &bins[rel];
     if (e < *slot)
         atomicMin(slot, e);
@@ -221,7 +223,7 @@ __device__ __forceinline__ void column_w(const uint4* v, const u32* rid, u32 j, 
 // loads then overlap instead of forming one dependent chain.
 template <int DT, int NP, bool ONE>
 __device__ __forceinline__ void fold_group(const uint4* x, const u32* rid, u32 j, uint4 lab, u32 A,
-                                           u32 b0, u32 nb, u64* bins)
+                                           u32 b0, u32 nb, u64* bins, u32 n)
 {
     u32 L[4] = {lab.x, lab.y, lab.z, lab.w};
     u64 e[4];
@@ -242,7 +244,7 @@ __device__ __forceinline__ void fold_group(const uint4* x, const u32* rid, u32 j
                 bi = rid[q];
             }
         }
-        e[c] = pack_edge(bk, bi, j + c);
+        e[c] = pack_edge(bk, bi, j + c, n);
     }
     u64 cur[4];
 #pragma unroll
@@ -292,7 +294,7 @@ __device__ __forceinline__ void contract_cols_w(const u32* __restrict__ Wp, u32 
             for (int u = 0; u < U; ++u) {
                 const u32 g = g0 + u * bd;
                 if (g < n4)
-                    fold_group<DT, NR, false>(v[u], rid, 4 * g, lab[u], A, b0, nb, bins);
+                    fold_group<DT, NR, false>(v[u], rid, 4 * g, lab[u], A, b0, nb, bins, cr);
             }
         }
         jt = 4 * n4;
@@ -303,7 +305,7 @@ __device__ __forceinline__ void contract_cols_w(const u32* __restrict__ Wp, u32 
 #pragma unroll
         for (int q = 1; q < NR; ++q)
             x[q].x = ((u32)q < np) ? ld_stream_u32(rp[q] + j) : x[0].x;
-        column_w<DT, NR, 0>(x, rid, j, label[j], A, b0, nb, bins);
+        column_w<DT, NR, 0>(x, rid, j, label[j], A, b0, nb, bins, cr);
     }
 }
 
@@ -315,7 +317,7 @@ __device__ __forceinline__ void contract_cols_w(const u32* __restrict__ Wp, u32 
 // row is always left of the column, so (row, column) is already (lo, hi).
 template <int DT, bool MASK>
 __device__ __forceinline__ void fold_upper(const uint4* v, const u32* rid, u32 j, uint4 lab, u32 A,
-                                           u32 b0, u32 nb, u64* bins)
+                                           u32 b0, u32 nb, u64* bins, u32 n)
 {
     constexpr int NR = 4;
     const u32 L[4] = {lab.x, lab.y, lab.z, lab.w};
@@ -336,7 +338,7 @@ __device__ __forceinline__ void fold_upper(const uint4* v, const u32* rid, u32 j
                 bi = rid[q];
             }
         }
-        e[c] = ((u64)bk << 32) | (bi << 16) | col;
+        e[c] = ((u64)bk << 32) | pair_code(bi, col, n);
     }
     u64 cur[4];
 #pragma unroll
@@ -383,9 +385,9 @@ __device__ __forceinline__ void contract_cols_w_upper(const u32* __restrict__ Wp
             v[q] = ((u32)q < np && j + 3 > rid[q]) ? ld_stream_v4(rp[q] + j) : v[0];
         const uint4 lab = *reinterpret_cast<const uint4*>(label + j);
         if (j > rmax)
-            fold_upper<DT, false>(v, rid, j, lab, A, b0, nb, bins);
+            fold_upper<DT, false>(v, rid, j, lab, A, b0, nb, bins, cr);
         else
-            fold_upper<DT, true>(v, rid, j, lab, A, b0, nb, bins);
+            fold_upper<DT, true>(v, rid, j, lab, A, b0, nb, bins, cr);
     }
 }
 

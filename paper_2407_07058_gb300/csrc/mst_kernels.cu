@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_rowmin(const u32* __restrict__ W, u32 n
         }
         m = block_min_u64(m, sh);
         if (threadIdx.x == 0)
-            best[row] = pack_edge((u32)(m >> 32), row, (u32)m & 0xFFFFu);
+            best[row] = pack_edge((u32)(m >> 32), row, (u32)m, n);
     }
 }
 
@@ -148,13 +148,13 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
 #pragma unroll
         for (int c = 0; c < 4; ++c)
             if (ci[c] != 0xFFFFFFFFu)
-                atomicMin(&best[j + c], pack_edge(ck[c], ci[c], j + c));
+                atomicMin(&best[j + c], pack_edge(ck[c], ci[c], j + c, n));
     }
     __syncthreads();
     for (u32 r = threadIdx.x; r < RS_ROWS && i0 + r < n; r += blockDim.x) {
         u64 x = s_row[r];
         if (x != EDGE_INF)
-            atomicMin(&best[i0 + r], pack_edge((u32)(x >> 32), i0 + r, (u32)x));
+            atomicMin(&best[i0 + r], pack_edge((u32)(x >> 32), i0 + r, (u32)x, n));
     }
 }
 
@@ -220,6 +220,76 @@ __global__ void __launch_bounds__(TWO ? CONTRACT_THREADS2 : CONTRACT_THREADS, TW
         if (item >= total)
             break;
         contract_item<DT, LEVEL0, VEC, UPPER>(a, item, cr, cn, total_chunks, bins, s_rows, s_red);
+    }
+}
+
+// Every level from the third on, in one cooperative launch (the first two
+// keep their own kernels: the passes over W or the points, the column minima
+// of P and the symmetrization of C_2).  Per level: the step, on the whole
+// grid while the matrix has more than STEP_BLOCK_MAX_C rows and on CTA 0
+// alone below that (the other CTAs wait at the grid barrier, whose bounded
+// wait covers it), then the contraction with every CTA taking items, then a
+// grid barrier.  The loop ends at the level that leaves one component, so no
+// launch is spent on rounds with nothing to do.
+constexpr u32 LEVELS_THREADS = 512;
+
+struct LevelsArgs {
+    StepArgs sa;       // fields shared by the levels; level, best_in/out, cnext set per level
+    ContractArgs ca;   // likewise; level, cin, cout, best_out set per level
+    u64* cb[2];        // C_1, C_3, ... and C_2, C_4, ...
+    u64* best[2];
+    int first, last;   // the levels [first, last)
+};
+
+__global__ void __launch_bounds__(LEVELS_THREADS, 1) k_levels(LevelsArgs a)
+{
+    extern __shared__ __align__(16) u64 bins[];
+    __shared__ u32 s_item, s_rows[CONTRACT_ROWS];
+    __shared__ u64 s_red[32];
+    Counters* ctr = a.sa.ctr;
+    GridTeam grid{&ctr->bar, a.sa.status};
+    for (int r = a.first; r < a.last; ++r) {
+        if (*(volatile u32*)&ctr->done)   // read after a grid barrier: the same in every CTA
+            break;
+        StepArgs sa = a.sa;
+        sa.level = r;
+        sa.best_in = a.best[r & 1];
+        sa.best_out = a.best[(r + 1) & 1];
+        sa.cnext = a.cb[r & 1];
+        const u32 cr = ((volatile u32*)ctr->c)[r];
+        if (cr > STEP_BLOCK_MAX_C) {
+            step_body(grid, sa);
+        } else if (blockIdx.x == 0) {
+            sa.update_comp = 0;   // the contraction below maps comp[] on the whole grid
+            BlockTeam bt;
+            step_body(bt, sa);
+        }
+        if (!grid.sync())
+            return;
+        if (*(volatile u32*)&ctr->done)
+            break;
+        ContractArgs ca = a.ca;
+        ca.level = r;
+        ca.cin = a.cb[(r - 1) & 1];
+        ca.cout = a.cb[r & 1];
+        ca.best_out = a.best[(r + 1) & 1];
+        const u32 cn = ((volatile u32*)ctr->c)[r + 1];
+        if (cr <= ca.comp_max_c)
+            for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < ca.n; v += gridDim.x * blockDim.x)
+                ca.comp[v] = ca.label[ca.comp[v]];
+        const u32 total_chunks = *(volatile u32*)&ctr->total_chunks;
+        const u32 total = total_chunks * ((cn + ca.bin_cap - 1) / ca.bin_cap);
+        for (;;) {
+            if (threadIdx.x == 0)
+                s_item = atomicAdd(&ctr->item_next, 1u);
+            __syncthreads();
+            const u32 item = s_item;
+            if (item >= total)
+                break;
+            contract_item<0, 0, false>(ca, item, cr, cn, total_chunks, bins, s_rows, s_red);
+        }
+        if (!grid.sync())
+            return;
     }
 }
 
@@ -358,6 +428,23 @@ cudaError_t set_smem(K kern, size_t bytes)
 
 }  // namespace
 
+__global__ void k_mst_split(const u64* __restrict__ mst, u32 n, u32* __restrict__ keys, u32* __restrict__ lo,
+                            u32* __restrict__ hi)
+{
+    for (u32 e = blockIdx.x * blockDim.x + threadIdx.x; e + 1 < n; e += gridDim.x * blockDim.x) {
+        const u64 x = mst[e];
+        keys[e] = edge_key(x);
+        edge_ends(x, n, lo + e, hi + e);
+    }
+}
+
+cudaError_t launch_mst_split(const u64* mst, u32 n, u32* keys, u32* lo, u32* hi, cudaStream_t s)
+{
+    const u32 m = n - 1, grid = (m + 255) / 256 < 1024 ? (m + 255) / 256 : 1024;
+    k_mst_split<<<grid, 256, 0, s>>>(mst, n, keys, lo, hi);
+    return cudaGetLastError();
+}
+
 cudaError_t preload_mst()
 {
     return touch_kernels(k_rowmin<0>, k_rowmin<1>, k_rowmin<2>, k_rowmin<3>, k_rowmin_sym<0>, k_rowmin_sym<1>,
@@ -370,7 +457,7 @@ cudaError_t preload_mst()
                          k_contract<2, 1, false, false, true>, k_contract<3, 1, false, false, true>,
                          k_contract<0, 1, false, false, false>, k_contract<1, 1, false, false, false>,
                          k_contract<2, 1, false, false, false>, k_contract<3, 1, false, false, false>,
-                         k_contract<0, 0, false, false, true>);
+                         k_contract<0, 0, false, false, true>, k_mst_split, k_levels);
 }
 
 cudaError_t preload_kernels()
@@ -386,6 +473,8 @@ cudaError_t preload_kernels()
         e = preload_batched();
     if (e == cudaSuccess)
         e = preload_points();
+    if (e == cudaSuccess)
+        e = preload_insert_tree();
     return e;
 }
 
@@ -463,7 +552,9 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
     if ((err = set_smem(k0a, smem2)) != cudaSuccess || (err = set_smem(k0b, smem)) != cudaSuccess ||
         (err = set_smem(k1, smem2)) != cudaSuccess || (err = set_smem(k_sym, sym_smem_bytes())) != cudaSuccess)
         return err;
-    for (int r = 0; r < ws.levels; ++r) {
+    // levels 0 and 1 here; every later level in one persistent launch below
+    const int direct_levels = ws.levels < 2 ? ws.levels : 2;
+    for (int r = 0; r < direct_levels; ++r) {
         StepArgs sa;
         sa.level = r;
         sa.n = n;
@@ -532,11 +623,15 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         ContractArgs ca1 = ca;
         ca.bin_cap = ws.bin_cap2;
         if (r == 0 && ps) {
-            // the point set's level 0: every distance computed once per bin range
-            ContractArgs cap = ca;
-            cap.bin_cap = ws.bin_cap_p;
-            if ((err = launch_contract_pts(cap, ps->P, ps->D, dt, ws.contract_blocks, s)) != cudaSuccess)
+            // the point set's level 0: coordinates in component order, then
+            // each group against every later group's contiguous columns
+            if ((err = launch_pts_gather(ps->P, ps->D, ws.members, ws.label, n, ps->Ps, ps->pvid, ps->pcomp,
+                                         s)) != cudaSuccess)
                 return err;
+            if ((err = launch_contract_pts_sorted(ca, ps->Ps, ps->pvid, ps->pcomp, ps->D, dt, 3 * ws.contract_blocks,
+                                                  s)) != cudaSuccess)
+                return err;
+            prof_launches(2);
         } else if (r == 0 && vec && ws.bin_cap_t > 0) {
             // upper triangle streamed by bulk copies while |C_1| fits beside
             // the copy ring, else one CTA per SM with all bins
@@ -569,6 +664,62 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         }
         prof_end(ph, s);
         if ((err = cudaGetLastError()) != cudaSuccess)
+            return err;
+    }
+    if (ws.levels > 2) {
+        LevelsArgs la;
+        StepArgs& sa = la.sa;
+        sa.level = 2;
+        sa.n = n;
+        sa.comp = ws.comp;
+        sa.hook = ws.hook;
+        sa.par = ws.par;
+        sa.flag = ws.flag;
+        sa.rootid = ws.rootid;
+        sa.label = ws.label;
+        sa.cnt = ws.cnt;
+        sa.fillc = ws.fillc;
+        sa.gstart = ws.gstart;
+        sa.members = ws.members;
+        sa.nchunk = ws.nchunk;
+        sa.chunk_start = ws.chunk_start;
+        sa.item_group = ws.item_group;
+        sa.mst = ws.mst;
+        sa.part = ws.part;
+        sa.ctr = ws.ctr;
+        sa.status = status;
+        sa.bin_cap = ws.bin_cap2;
+        sa.label16 = nullptr;
+        ContractArgs& ca = la.ca;
+        ca.level = 2;
+        ca.label = ws.label;
+        ca.members = ws.members;
+        ca.gstart = ws.gstart;
+        ca.nchunk = ws.nchunk;
+        ca.chunk_start = ws.chunk_start;
+        ca.item_group = ws.item_group;
+        ca.ctr = ws.ctr;
+        ca.bin_cap = ws.bin_cap2;
+        ca.comp = ws.comp;
+        ca.n = n;
+        ca.comp_max_c = STEP_BLOCK_MAX_C;
+        la.cb[0] = cb[0];
+        la.cb[1] = cb[1];
+        la.best[0] = ws.best[0];
+        la.best[1] = ws.best[1];
+        la.first = 2;
+        la.last = ws.levels;
+        if ((err = set_smem(k_levels, smem2)) != cudaSuccess)
+            return err;
+        if ((err = cudaMemsetAsync(&ws.ctr->bar, 0, 2 * sizeof(u32), s)) != cudaSuccess)
+            return err;
+        void* args[] = {&la};
+        prof_begin(PH_CONTRACT, s);
+        err = cudaLaunchCooperativeKernel((const void*)k_levels, dim3(ws.coop_blocks), dim3(LEVELS_THREADS), args,
+                                          smem2, s);
+        prof_end(PH_CONTRACT, s);
+        prof_launches(1);
+        if (err != cudaSuccess)
             return err;
     }
     // the point set's tree carries keys of squared distances: convert them

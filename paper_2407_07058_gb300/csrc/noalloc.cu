@@ -52,6 +52,7 @@ struct NoallocWs {
     u64* mxo;
     u32* nha;
     u64 *skey0, *skey1;
+    u32 *sval0, *sval1;
     u32 *hist, *first_child, *next_sib, *pos, *order, *nsize, *gap, *st;
     u64* cscratch;   // contraction matrices (used when M == W)
     u32* status;     // device-detected errors of this entry point (sticky until
@@ -74,7 +75,7 @@ __device__ void noalloc_rowmin(const u32* __restrict__ W, u32 n, u64* __restrict
         }
         m = warp_min_u64(m);
         if (lane == 0)
-            best[i] = pack_edge((u32)(m >> 32), i, (u32)m & 0xFFFFu);
+            best[i] = pack_edge((u32)(m >> 32), i, (u32)m, n);
     }
 }
 
@@ -190,6 +191,8 @@ __device__ void noalloc_solve(const NoallocWs& w, const u32* W, u32* M, u32 n, u
     la.nha = w.nha;
     la.skey0 = w.skey0;
     la.skey1 = w.skey1;
+    la.sval0 = w.sval0;
+    la.sval1 = w.sval1;
     la.hist = w.hist;
     la.ntiles = (n - 1 + 2047) / 2048;
     la.first_child = w.first_child;
@@ -287,6 +290,8 @@ cudaError_t noalloc_setup(int dev, NoallocDev& d)
     s.nha = w.nha;
     s.skey0 = w.skey[0];
     s.skey1 = w.skey[1];
+    s.sval0 = w.sval[0];
+    s.sval1 = w.sval[1];
     s.hist = w.hist;
     s.first_child = w.first_child;
     s.next_sib = w.next_sib;

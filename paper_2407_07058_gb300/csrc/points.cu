@@ -60,6 +60,23 @@ __device__ __forceinline__ void load_pt(const float* __restrict__ p, float (&x)[
     }
 }
 
+// A squared distance is +0 or positive (finite coordinates), so its bits
+// order it; the widest order reverses that.  sbits_order gives a value whose
+// unsigned order is the key order, and order_to_key the key itself:
+// key_of(bits, DT) is bits | 0x80000000 for DT = 0 and ~(bits | 0x80000000)
+// = ~bits & 0x7FFFFFFF for DT = 2, both monotone in the value below.
+template <int DT>
+__device__ __forceinline__ u32 sbits_order(float s)
+{
+    return (DT & 2) ? ~__float_as_uint(s) : __float_as_uint(s);
+}
+
+template <int DT>
+__device__ __forceinline__ u32 order_to_key(u32 u)
+{
+    return (DT & 2) ? (u & 0x7FFFFFFFu) : (u | 0x80000000u);
+}
+
 // columns per thread of the contraction (512 threads, up to 128 registers):
 // the columns' coordinates take 16..32 registers
 template <int D>
@@ -133,24 +150,40 @@ __global__ void __launch_bounds__(RP_THREADS, 2)
     for (int c = 0; c < CPL; ++c)
         ck[c] = ci[c] = 0xFFFFFFFFu;
     const bool any = j < n;
+    // no mask where every column of the tile lies right of every row and below n
+    const bool clear = c0 >= imax && c0 + TCOLS <= n;
+    // (the order values below are the keys' order; see sbits_order)
     for (u32 i = imax; i-- > i0;) {
         float rx[D];
 #pragma unroll
         for (int k = 0; k < D; ++k)
             rx[k] = s_pts[(i - i0) * D + k];
         u32 rk = 0xFFFFFFFFu, rj = 0xFFFFFFFFu;
-        if (any && j + CPL - 1 > i) {
+        if (clear) {
+#pragma unroll
+            for (int c = CPL - 1; c >= 0; --c) {
+                const u32 u = sbits_order<DT>(sq_dist<D>(rx, cx[c]));
+                if (u <= rk) {
+                    rk = u;
+                    rj = j + c;
+                }
+                if (u <= ck[c]) {
+                    ck[c] = u;
+                    ci[c] = i;
+                }
+            }
+        } else if (any && j + CPL - 1 > i) {
 #pragma unroll
             for (int c = CPL - 1; c >= 0; --c) {
                 const u32 col = j + c;
-                const u32 k = key_of(__float_as_uint(sq_dist<D>(rx, cx[c])), DT);
+                const u32 u = sbits_order<DT>(sq_dist<D>(rx, cx[c]));
                 const bool ok = col > i && col < n;
-                if (ok && k <= rk) {
-                    rk = k;
+                if (ok && u <= rk) {
+                    rk = u;
                     rj = col;
                 }
-                if (ok && k <= ck[c]) {
-                    ck[c] = k;
+                if (ok && u <= ck[c]) {
+                    ck[c] = u;
                     ci[c] = i;
                 }
             }
@@ -158,17 +191,17 @@ __global__ void __launch_bounds__(RP_THREADS, 2)
         const u32 kmin = __reduce_min_sync(0xFFFFFFFFu, rk);
         const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, rk == kmin ? rj : 0xFFFFFFFFu);
         if (lane == 0 && jmin != 0xFFFFFFFFu)
-            atomicMin(&s_row[i - i0], ((u64)kmin << 32) | jmin);
+            atomicMin(&s_row[i - i0], ((u64)order_to_key<DT>(kmin) << 32) | jmin);
     }
 #pragma unroll
     for (int c = 0; c < CPL; ++c)
         if (ci[c] != 0xFFFFFFFFu)
-            atomicMin(&best[j + c], pack_edge(ck[c], ci[c], j + c));
+            atomicMin(&best[j + c], pack_edge(order_to_key<DT>(ck[c]), ci[c], j + c, n));
     __syncthreads();
     for (u32 r = threadIdx.x; r < RP_ROWS && i0 + r < n; r += blockDim.x) {
         const u64 x = s_row[r];
         if (x != EDGE_INF)
-            atomicMin(&best[i0 + r], pack_edge((u32)(x >> 32), i0 + r, (u32)x));
+            atomicMin(&best[i0 + r], pack_edge((u32)(x >> 32), i0 + r, (u32)x, n));
     }
 }
 
@@ -275,7 +308,7 @@ __global__ void __launch_bounds__(CP_THREADS, 1) k_contract_pts(ContractArgs a, 
                 const u32 rel = L - b0;
                 if (L == A || rel >= nb)
                     continue;
-                const u64 e = ((u64)bk[c] << 32) | ((u64)bi[c] << 16) | col;
+                const u64 e = ((u64)bk[c] << 32) | pair_code(bi[c], col, cr);
                 if (e < bins[rel])
                     atomicMin(&bins[rel], e);
             }
@@ -295,6 +328,188 @@ __global__ void __launch_bounds__(CP_THREADS, 1) k_contract_pts(ContractArgs a, 
         m = block_min_u64(m, s_red);
         if (tid == 0 && m != EDGE_INF)
             atomicMin(&a.best_out[A], m);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------ level 0, sorted columns
+// After the level-0 step the members list holds the vertices grouped by
+// component (group A at positions gstart[A] .. gstart[A+1]).  k_pts_gather
+// copies the coordinates into that order (Ps), with each position's vertex
+// (pvid) and component (pcomp).  k_contract_pts_sorted then takes group A's
+// rows against every later position: those columns belong to groups B > A,
+// each group's columns contiguous, so P'(A, B) = min over the run of B's
+// columns of the column minima -- a run reduction instead of a bin array.
+// Row A of P' holds INF for B <= A, so C_1(A, B) = min(P'(A, B), P'(B, A))
+// as for the upper-triangle P of a stored W, and the same column minima and
+// level-1 symmetrization follow.
+__global__ void k_pts_gather(const float* __restrict__ P, int D, const u32* __restrict__ members,
+                             const u32* __restrict__ label, u32 n, float* __restrict__ Ps,
+                             u32* __restrict__ pvid, u32* __restrict__ pcomp)
+{
+    for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const u32 v = members[q];
+        pvid[q] = v;
+        pcomp[q] = label[v];
+        for (int k = 0; k < D; ++k)
+            Ps[(size_t)q * D + k] = P[(size_t)v * D + k];
+    }
+}
+
+constexpr u32 CS_THREADS = 256;
+constexpr u32 CS_ROWCAP = 256;   // rows of a group kept in shared memory
+
+template <int D>
+constexpr int cols_sorted()
+{
+    return D <= 4 ? 8 : (D == 8 ? 4 : (D == 16 ? 2 : 1));
+}
+
+template <int DT, int D>
+__global__ void __launch_bounds__(CS_THREADS, 3)
+    k_contract_pts_sorted(ContractArgs a, const float* __restrict__ Ps, const u32* __restrict__ pvid,
+                          const u32* __restrict__ pcomp)
+{
+    constexpr int CPC = cols_sorted<D>();
+    constexpr u32 CH = CS_THREADS * CPC;   // columns per chunk
+    __shared__ __align__(16) float s_rp[CS_ROWCAP * D];
+    __shared__ u32 s_rv[CS_ROWCAP];
+    __shared__ u64 s_e[CH];
+    __shared__ u32 s_b[CH];
+    __shared__ u32 s_item;
+    __shared__ u64 s_carry_e[2];
+    __shared__ u32 s_carry_b[2];
+    __shared__ u64 s_red[32];
+    Counters* ctr = a.ctr;
+    if (*(volatile u32*)&ctr->done)
+        return;
+    const u32 n = ((volatile u32*)ctr->c)[0];
+    const u32 cn = ((volatile u32*)ctr->c)[1];
+    const u32 tid = threadIdx.x;
+    if (n <= a.comp_max_c)
+        for (u32 v = blockIdx.x * blockDim.x + tid; v < a.n; v += gridDim.x * blockDim.x)
+            a.comp[v] = a.label[a.comp[v]];
+    for (;;) {
+        if (tid == 0)
+            s_item = atomicAdd(&ctr->item_next, 1u);
+        __syncthreads();
+        const u32 A = s_item;
+        if (A >= cn)
+            break;
+        const u32 g0 = a.gstart[A], g1 = a.gstart[A + 1];
+        const u32 nrows = g1 - g0;
+        const bool rows_in_smem = nrows <= CS_ROWCAP;
+        if (rows_in_smem) {
+            for (u32 e = tid; e < nrows * D; e += CS_THREADS)
+                s_rp[e] = Ps[(size_t)g0 * D + e];
+            for (u32 r = tid; r < nrows; r += CS_THREADS)
+                s_rv[r] = pvid[g0 + r];
+        }
+        u64* row = a.cout + (size_t)A * cn;
+        for (u32 b = tid; b <= A; b += CS_THREADS)   // no pairs with groups B <= A
+            row[b] = EDGE_INF;
+        if (tid == 0) {
+            s_carry_b[0] = 0xFFFFFFFFu;
+            s_carry_e[0] = EDGE_INF;
+        }
+        u64 mrow = EDGE_INF;   // this thread's part of row A's minimum
+        __syncthreads();
+        int cur = 0;
+        for (u32 q0 = g1; q0 < n; q0 += CH) {
+            // 1. each column's smallest (key, row vertex) over the group's rows
+            const u32 qt = q0 + tid * CPC;
+            float cx[CPC][D];
+            u32 bk[CPC], bv[CPC], vq[CPC];
+#pragma unroll
+            for (int c = 0; c < CPC; ++c) {
+                const u32 q = qt + c;
+                if (q < n) {
+                    load_pt<D>(Ps + (size_t)q * D, cx[c]);
+                    vq[c] = pvid[q];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < D; ++k)
+                        cx[c][k] = 0.0f;
+                    vq[c] = 0u;
+                }
+                bk[c] = bv[c] = 0xFFFFFFFFu;
+            }
+            for (u32 r = 0; r < nrows; ++r) {
+                float rx[D];
+                u32 vr;
+                if (rows_in_smem) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k)
+                        rx[k] = s_rp[r * D + k];
+                    vr = s_rv[r];
+                } else {
+                    load_pt<D>(Ps + (size_t)(g0 + r) * D, rx);
+                    vr = pvid[g0 + r];
+                }
+#pragma unroll
+                for (int c = 0; c < CPC; ++c) {
+                    const u32 u = sbits_order<DT>(sq_dist<D>(rx, cx[c]));
+                    if (u < bk[c] || (u == bk[c] && vr < bv[c])) {
+                        bk[c] = u;
+                        bv[c] = vr;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CPC; ++c) {
+                const u32 q = qt + c;
+                const u32 i = tid * CPC + c;
+                if (q < n && bv[c] != 0xFFFFFFFFu) {
+                    s_e[i] = ((u64)order_to_key<DT>(bk[c]) << 32) |
+                             pair_code(min(bv[c], vq[c]), max(bv[c], vq[c]), n);
+                    s_b[i] = pcomp[q];
+                } else {
+                    s_e[i] = EDGE_INF;
+                    s_b[i] = q < n ? pcomp[q] : 0xFFFFFFFFu;
+                }
+            }
+            __syncthreads();
+            // 2. one thread per run of equal B in the chunk reduces it; the
+            // run that reaches the chunk's end is carried into the next chunk
+            const u32 ncol = min(CH, n - q0);
+            const u32 cb = s_carry_b[cur];
+            const u64 ce = s_carry_e[cur];
+            for (u32 i = tid; i < ncol; i += CS_THREADS) {
+                const u32 B = s_b[i];
+                if (i > 0 && s_b[i - 1] == B)
+                    continue;   // not a run start
+                u64 v = EDGE_INF;
+                u32 j = i;
+                for (; j < ncol && s_b[j] == B; ++j)
+                    v = s_e[j] < v ? s_e[j] : v;
+                if (i == 0) {
+                    if (cb == B) {
+                        v = ce < v ? ce : v;
+                    } else if (cb != 0xFFFFFFFFu) {
+                        row[cb] = ce;   // the carried run ended with the last chunk
+                        mrow = ce < mrow ? ce : mrow;
+                    }
+                }
+                if (j < ncol) {
+                    row[B] = v;
+                    mrow = v < mrow ? v : mrow;
+                } else {
+                    s_carry_b[cur ^ 1] = B;
+                    s_carry_e[cur ^ 1] = v;
+                }
+            }
+            cur ^= 1;
+            __syncthreads();
+        }
+        // the last run of the item
+        if (tid == 0 && s_carry_b[cur] != 0xFFFFFFFFu) {
+            const u64 v = s_carry_e[cur];
+            row[s_carry_b[cur]] = v;
+            mrow = v < mrow ? v : mrow;
+        }
+        mrow = block_min_u64(mrow, s_red);
+        if (tid == 0 && mrow != EDGE_INF)
+            atomicMin(&a.best_out[A], mrow);
         __syncthreads();
     }
 }
@@ -410,6 +625,35 @@ cudaError_t launch_contract_pts(const ContractArgs& ca, const float* P, int D, i
     return (dt & 2) ? contract_pts_dt<2>(ca, P, D, blocks, smem, s) : contract_pts_dt<0>(ca, P, D, blocks, smem, s);
 }
 
+cudaError_t launch_pts_gather(const float* P, int D, const u32* members, const u32* label, u32 n, float* Ps,
+                              u32* pvid, u32* pcomp, cudaStream_t s)
+{
+    const u32 grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    k_pts_gather<<<grid, 256, 0, s>>>(P, D, members, label, n, Ps, pvid, pcomp);
+    return cudaGetLastError();
+}
+
+template <int DT>
+static cudaError_t contract_sorted_dt(const ContractArgs& ca, const float* Ps, const u32* pvid, const u32* pcomp,
+                                      int D, int blocks, cudaStream_t s)
+{
+    switch (D) {
+    case 2: k_contract_pts_sorted<DT, 2><<<blocks, CS_THREADS, 0, s>>>(ca, Ps, pvid, pcomp); break;
+    case 4: k_contract_pts_sorted<DT, 4><<<blocks, CS_THREADS, 0, s>>>(ca, Ps, pvid, pcomp); break;
+    case 8: k_contract_pts_sorted<DT, 8><<<blocks, CS_THREADS, 0, s>>>(ca, Ps, pvid, pcomp); break;
+    case 16: k_contract_pts_sorted<DT, 16><<<blocks, CS_THREADS, 0, s>>>(ca, Ps, pvid, pcomp); break;
+    default: k_contract_pts_sorted<DT, 32><<<blocks, CS_THREADS, 0, s>>>(ca, Ps, pvid, pcomp); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_pts_sorted(const ContractArgs& ca, const float* Ps, const u32* pvid,
+                                       const u32* pcomp, int D, int dt, int blocks, cudaStream_t s)
+{
+    return (dt & 2) ? contract_sorted_dt<2>(ca, Ps, pvid, pcomp, D, blocks, s)
+                    : contract_sorted_dt<0>(ca, Ps, pvid, pcomp, D, blocks, s);
+}
+
 cudaError_t launch_mst_sqrt(u64* mst, u32 m, int dt, cudaStream_t s)
 {
     if (m == 0)
@@ -430,7 +674,11 @@ cudaError_t preload_points()
                          k_contract_pts<0, 4>, k_contract_pts<0, 8>, k_contract_pts<0, 16>,
                          k_contract_pts<0, 32>, k_contract_pts<2, 2>, k_contract_pts<2, 4>,
                          k_contract_pts<2, 8>, k_contract_pts<2, 16>, k_contract_pts<2, 32>, k_mst_sqrt<0>,
-                         k_mst_sqrt<2>);
+                         k_mst_sqrt<2>, k_pts_gather, k_contract_pts_sorted<0, 2>, k_contract_pts_sorted<0, 4>,
+                         k_contract_pts_sorted<0, 8>, k_contract_pts_sorted<0, 16>,
+                         k_contract_pts_sorted<0, 32>, k_contract_pts_sorted<2, 2>,
+                         k_contract_pts_sorted<2, 4>, k_contract_pts_sorted<2, 8>,
+                         k_contract_pts_sorted<2, 16>, k_contract_pts_sorted<2, 32>);
 }
 
 }  // namespace appd

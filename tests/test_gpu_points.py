@@ -78,7 +78,7 @@ def test_points_full_size_every_row():
     torch.cuda.synchronize()
     assert appd.last_device_status() == 0
     W = oracle.points_w(X)
-    order, mst = oracle.prim(W)
+    order, mst = oracle.prim_sym(W)   # the definition is symmetric bit for bit
     for r0 in range(0, n, 4096):
         ref = oracle.prim_rows(W, order, mst, np.arange(r0, r0 + 4096))
         assert_bits(M[r0: r0 + 4096].cpu().numpy(), ref, f"points n={n} rows {r0}..")
@@ -92,6 +92,6 @@ def test_points_argument_errors():
     assert lib.appd_solve_points(X.data_ptr(), 10, 0, appd.F32, M.data_ptr(), st) == 1
     assert lib.appd_solve_points(X.data_ptr(), 10, 33, appd.F32, M.data_ptr(), st) == 1
     assert lib.appd_solve_points(X.data_ptr(), 10, 4, appd.U32, M.data_ptr(), st) == 1
-    assert lib.appd_solve_points(X.data_ptr(), 65537, 4, appd.F32, M.data_ptr(), st) == 2
+    assert lib.appd_solve_points(X.data_ptr(), 92683, 4, appd.F32, M.data_ptr(), st) == 2
     assert lib.appd_solve_points(X.data_ptr(), 10, 4, appd.F32, X.data_ptr(), st) == 8
     assert lib.appd_solve_points(X.data_ptr(), 0, 4, appd.F32, M.data_ptr(), st) == 0

@@ -43,13 +43,18 @@ def test_argument_errors_need_no_gpu():
     assert lib.appd_solve(fake, 4, 0, None, None) == 1          # null M
     assert lib.appd_solve(fake, -1, 0, fake2, None) == 1        # n < 0
     assert lib.appd_solve(fake, 4, 7, fake2, None) == 1         # bad dtype
-    assert lib.appd_solve(fake, 65537, 0, fake2, None) == 2     # too large
+    assert lib.appd_solve(fake, 92683, 0, fake2, None) == 2     # too large (n (n-1) / 2 > 2^32)
     assert lib.appd_solve(fake, 0, 0, fake2, None) == 0         # n == 0: no-op
     # partial overlap of M and W (M == W exactly is allowed)
     assert lib.appd_solve(ctypes.c_void_p(0x10000), 64, 0, ctypes.c_void_p(0x10000 + 64), None) == 8
-    assert lib.appd_solve_alg4(fake, 65537, 1, fake2, None) == 2
+    assert lib.appd_solve_alg4(fake, 92683, 1, fake2, None) == 2
     assert lib.appd_mst(None, 4, 0, fake, None) == 1
-    assert lib.appd_leaf_order(fake, 70000, 0, fake2, fake2, None) == 2
+    assert lib.appd_mst(fake, 65537, 0, fake2, None) == 2       # 16-bit endpoints in this format
+    assert lib.appd_mst_edges(fake, 92683, 0, fake2, fake2, fake2, None) == 2
+    assert lib.appd_mst_edges(fake, 10, 0, None, fake2, fake2, None) == 1
+    assert lib.appd_leaf_order(fake, 92683, 0, fake2, fake2, None) == 2
+    assert lib.appd_insert_vertex(fake, 92682, 0, fake2, ctypes.c_void_p(0x10 << 40), None) == 2
+    assert lib.appd_solve_points(fake, 92683, 2, 0, fake2, None) == 2
     assert lib.appd_check_symmetric(None, 4, 0, None) == 1
     assert lib.appd_solve_batched(None, None, None, None, None, -1, None) == 1
     assert lib.appd_batched_get_tuning(None, None, None) == 1

@@ -473,3 +473,56 @@ def test_points_w_vs_fp64_generator_on_integer_points():
     assert bits_equal(W, synth.euclid(X))
     assert bits_equal(W, np.ascontiguousarray(W.T))
     assert not np.any(np.diag(W).view(np.uint32))
+
+
+# ------------------------------- pair numbers of graphs above 65536 vertices
+def test_rank_pair_numbers_on_small_graphs():
+    # Graphs above 65536 vertices number a pair by its rank among all pairs in
+    # (lo, hi) order.  Forced onto small graphs, every routine that uses edge
+    # codes must still give the pinned matrix, and the codes must rank the
+    # pairs: code_ends inverts them and they sort as (key, lo, hi).
+    rng = np.random.default_rng(41)
+    cases = [sym_random(7, rng, np.float32), sym_random(40, rng, np.uint32, "ties"),
+             synth.euclid(synth.uniform_points(200, 2, seed=42)), synth.hash_u32(2, seed=43)]
+    refs = [threshold_connectivity(W) if W.shape[0] <= 40 else oracle.fw(W) for W in cases]
+    with oracle.short_limit(1):
+        for W, ref in zip(cases, refs):
+            n = W.shape[0]
+            assert bits_equal(oracle.appd(W), ref)
+            assert bits_equal(oracle.appd_ascending(W), ref)
+            order, mst = oracle.prim(W)
+            assert bits_equal(oracle.prim_rows(W, order, mst, np.arange(n)), ref)
+            assert bits_equal(oracle.tree_rows(W, mst, np.arange(n)), ref)
+            lo, hi = oracle.code_ends(mst, n)
+            assert np.all(lo < hi) and np.all(hi < n)
+            rank = lo.astype(np.int64) * (n - 1) - lo.astype(np.int64) * (lo.astype(np.int64) - 1) // 2 \
+                + (hi.astype(np.int64) - lo.astype(np.int64) - 1)
+            assert np.array_equal(mst & 0xFFFFFFFF, rank.astype(np.uint64))
+            K = keys_np(W)
+            assert np.array_equal(mst >> 32, K[lo, hi])
+        # every pair of a 300-vertex graph: the rank is a bijection onto
+        # 0 .. n(n-1)/2 - 1 that code_ends inverts
+        n = 300
+        ii, jj = np.triu_indices(n, 1)
+        r = (ii * (n - 1) - ii * (ii - 1) // 2 + (jj - ii - 1)).astype(np.uint64)
+        assert np.array_equal(np.sort(r), np.arange(n * (n - 1) // 2, dtype=np.uint64))
+        lo, hi = oracle.code_ends(r, n)
+        assert np.array_equal(lo, ii.astype(np.uint32)) and np.array_equal(hi, jj.astype(np.uint32))
+    # and the short form is back
+    order, mst = oracle.prim(cases[1])
+    assert np.array_equal((mst >> 16) & 0xFFFF, oracle.code_ends(mst, 40)[0])
+
+
+def test_prim_sym_equals_prim_on_symmetric_input():
+    rng = np.random.default_rng(44)
+    cases = [synth.euclid(synth.uniform_points(500, 2, seed=45)), synth.hash_u32(300, seed=46),
+             sym_random(64, rng, np.uint32, "ties"), sym_random(2, rng, np.float32)]
+    for W in cases:
+        for widest in (False, True):
+            o1, m1 = oracle.prim(W, widest=widest)
+            o2, m2 = oracle.prim_sym(W, widest=widest)
+            assert np.array_equal(o1, o2) and np.array_equal(m1, m2)
+        with oracle.short_limit(1):
+            o1, m1 = oracle.prim(W)
+            o2, m2 = oracle.prim_sym(W)
+            assert np.array_equal(o1, o2) and np.array_equal(m1, m2)
