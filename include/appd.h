@@ -292,9 +292,11 @@ appd_status appd_batched_tuning(int32_t ctas_per_sm, int32_t fill_rows, int64_t 
 
 /*
  * appd_batched_autotune -- picks the batched path's fill rows and size
- * cut-over for this GPU by timing every candidate pair (fill rows 64..512,
- * cut-over 512..4096) on a seeded synthetic batch of 192 graphs, installs the
- * fastest for this process, and appends it to the JSON-lines file cache_path
+ * cut-over for this GPU by timing every candidate pair (fill rows 256..2048,
+ * cut-over 512..4096), then the warp-Prim limit (0..512, see
+ * appd_batched_prim_max) with the best pair, on a seeded synthetic batch of
+ * 192 graphs, installs the fastest for this process, and appends it to the
+ * JSON-lines file cache_path
  * (keyed by GPU name and driver version; NULL: no cache).  If cache_path
  * already holds an entry for this GPU, it is installed without a search.
  * Synchronizes s; allocates 2.4 GB of device memory for the search and frees
@@ -306,6 +308,17 @@ appd_status appd_batched_autotune(const char *cache_path, appd_stream_t s);
 /* Reads the batched path's current parameters (see appd_batched_tuning);
  * APPD_ERR_INVALID on a null pointer.  Needs no GPU. */
 appd_status appd_batched_get_tuning(int32_t *ctas_per_sm, int32_t *fill_rows, int64_t *n_split);
+
+/*
+ * appd_batched_prim_max -- graphs of the batched path with at most prim_max
+ * vertices (0..512) are solved one per warp by Prim's algorithm (Section 3's
+ * MST step; its visiting order is the leaf order the fill reads), 16 graphs
+ * at once per CTA; larger ones by the one-CTA Boruvka solve.  Default 256;
+ * appd_batched_autotune searches it.  APPD_ERR_INVALID out of range.
+ * appd_batched_get_prim_max reads it.  (Scheduling of this library.)
+ */
+appd_status appd_batched_prim_max(int32_t prim_max);
+appd_status appd_batched_get_prim_max(int32_t *prim_max);
 
 /*
  * appd_check_symmetric -- returns APPD_OK if W(i,j) and W(j,i) have identical
@@ -372,7 +385,9 @@ int32_t appd_profile_end(double *out, int32_t cap);
 typedef struct appd_server appd_server;
 
 /* budget_bytes: device bytes the server may hold (slots + workspace).
- * max_inflight: upper bound on admitted, unreleased requests. */
+ * max_inflight: upper bound on admitted, unreleased requests.
+ * The server takes the batched path's parameters set for the process at
+ * creation (appd_batched_tuning / appd_batched_prim_max / autotune). */
 appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_server **out);
 
 /* Admit a request for an n-vertex graph of dtype dt.  On APPD_OK, *req_id is

@@ -28,7 +28,8 @@ EXPORTS = ["appd_status_str", "appd_solve", "appd_solve_points", "appd_solve_alg
            "appd_solve_host_async", "appd_solve_host_wait", "appd_solve_noalloc", "appd_insert_vertex", "appd_insert_vertex_tree", "appd_mst",
            "appd_mst_edges", "appd_leaf_order",
            "appd_solve_batched", "appd_batched_tuning", "appd_batched_autotune",
-           "appd_batched_get_tuning", "appd_check_symmetric",
+           "appd_batched_get_tuning", "appd_batched_prim_max", "appd_batched_get_prim_max",
+           "appd_check_symmetric",
            "appd_last_device_status", "appd_probe_bounded_wait", "appd_release_workspaces",
            "appd_debug_mark_failed", "appd_profile_begin",
            "appd_profile_end", "appd_server_create",
@@ -75,6 +76,8 @@ def load(build_if_missing: bool = True):
             "appd_batched_autotune": [ctypes.c_char_p, vp],
             "appd_batched_get_tuning": [ctypes.POINTER(i32), ctypes.POINTER(i32),
                                         ctypes.POINTER(i64)],
+            "appd_batched_prim_max": [i32],
+            "appd_batched_get_prim_max": [ctypes.POINTER(i32)],
             "appd_check_symmetric": [vp, i64, ci, vp],
             "appd_last_device_status": [vp],
             "appd_probe_bounded_wait": [i32, vp],
@@ -346,10 +349,16 @@ def batched_autotune(cache_path: str | None = None, stream=None) -> dict:
 
 
 def get_batched_tuning() -> dict:
-    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    a, b, c, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
     _check(load().appd_batched_get_tuning(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "appd_batched_get_tuning")
-    return {"ctas_per_sm": a.value, "fill_rows": b.value, "n_split": c.value}
+    _check(load().appd_batched_get_prim_max(ctypes.byref(d)), "appd_batched_get_prim_max")
+    return {"ctas_per_sm": a.value, "fill_rows": b.value, "n_split": c.value, "prim_max": d.value}
+
+
+def batched_prim_max(prim_max: int = 256):
+    """Largest batched graph solved by one warp with Prim (0..512)."""
+    _check(load().appd_batched_prim_max(prim_max), "appd_batched_prim_max")
 
 
 def release_workspaces():

@@ -132,7 +132,6 @@ cudaError_t appd::workspace_create(int64_t n, Workspace** out)
     nw->bin_cap = (u32)((smem_optin - 2048) / 8);
     nw->bin_cap2 = (u32)((smem_optin / 2 - 2048) / 8);
     nw->bin_cap_t = contract_tma_bin_cap(smem_optin);
-    nw->bin_cap_p = contract_pts_bin_cap(smem_optin);
     *out = nw;
     return cudaSuccess;
 }
@@ -969,6 +968,24 @@ appd_status appd_batched_tuning(int32_t ctas_per_sm, int32_t fill_rows, int64_t 
     g_tune.ctas_per_sm = ctas_per_sm;
     g_tune.fill_rows = fill_rows;
     g_tune.n_split = n_split;
+    return APPD_OK;
+}
+
+appd_status appd_batched_prim_max(int32_t prim_max)
+{
+    if (prim_max < 0 || prim_max > 512)
+        return APPD_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune.prim_max = (u32)prim_max;
+    return APPD_OK;
+}
+
+appd_status appd_batched_get_prim_max(int32_t* prim_max)
+{
+    if (!prim_max)
+        return APPD_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    *prim_max = (int32_t)g_tune.prim_max;
     return APPD_OK;
 }
 

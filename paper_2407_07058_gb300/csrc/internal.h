@@ -45,7 +45,6 @@ struct Workspace {
     u32 bin_cap = 0;         // u64 bins per contraction CTA (one CTA per SM)
     u32 bin_cap2 = 0;        // u64 bins per contraction CTA (two CTAs per SM)
     u32 bin_cap_t = 0;       // u64 bins beside the copy ring of the bulk-copy contraction
-    u32 bin_cap_p = 0;       // u64 bins of the point-set contraction (one CTA per SM)
     void* base = nullptr;
     size_t bytes = 0;
 
@@ -99,10 +98,7 @@ int points_dim(int d);
 u32 points_rows_padded(u32 n);
 cudaError_t launch_pts_pad(const float* X, u32 n, int d, float* P, cudaStream_t s);
 cudaError_t launch_rowmin_pts(const float* P, int D, u32 n, int dt, u64* best, cudaStream_t s);
-u32 contract_pts_bin_cap(int smem_optin);
 struct ContractArgs;
-cudaError_t launch_contract_pts(const ContractArgs& ca, const float* P, int D, int dt, int blocks,
-                                cudaStream_t s);
 cudaError_t launch_mst_sqrt(u64* mst, u32 m, int dt, cudaStream_t s);
 cudaError_t launch_pts_gather(const float* P, int D, const u32* members, const u32* label, u32 n, float* Ps,
                               u32* pvid, u32* pcomp, cudaStream_t s);

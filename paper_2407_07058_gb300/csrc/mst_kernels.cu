@@ -578,7 +578,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         sa.part = ws.part;
         sa.ctr = ws.ctr;
         sa.status = status;
-        sa.bin_cap = (r == 0 && ps) ? ws.bin_cap_p : ws.bin_cap;
+        sa.bin_cap = ws.bin_cap;
         // level 0 of the upper-triangle path also keeps 16-bit labels (every
         // component of round 1 has two or more vertices: ids < 32768)
         sa.label16 = (r == 0 && vec && ws.bin_cap_t > 0) ? ws.label16 : nullptr;

@@ -11,7 +11,7 @@
 //
 // Only the two passes that read W in the stored-matrix solve change: the
 // round-1 minima (k_rowmin_pts) and the level-0 contraction
-// (k_contract_pts), both over the upper triangle i < j.  They compare s
+// (k_pts_gather + k_contract_pts_sorted), both over the pairs i < j.  They compare s
 // instead of sqrt(s): the square root is monotone, so ordering edges by
 // (key(s), lo, hi) refines the order by W, and the spanning tree found is a
 // minimum spanning tree for W as well; the n - 1 tree edges' keys are then
@@ -75,14 +75,6 @@ template <int DT>
 __device__ __forceinline__ u32 order_to_key(u32 u)
 {
     return (DT & 2) ? (u & 0x7FFFFFFFu) : (u | 0x80000000u);
-}
-
-// columns per thread of the contraction (512 threads, up to 128 registers):
-// the columns' coordinates take 16..32 registers
-template <int D>
-constexpr int cols_per_thread()
-{
-    return D <= 4 ? 8 : (D == 8 ? 4 : (D == 16 ? 2 : 1));
 }
 
 // columns per lane of the round-1 tile (two 256-thread CTAs per SM, up to
@@ -205,144 +197,20 @@ __global__ void __launch_bounds__(RP_THREADS, 2)
     }
 }
 
-// The level-0 contraction of the points' graph over the upper triangle: the
-// same work items as k_contract (group A, at most CONTRACT_ROWS of its rows,
-// one bin range), the rows' coordinates in shared memory, every column j
-// right of the item's smallest row swept once per item with its coordinates
-// in registers.  For each column, the smallest key over the item's rows left
-// of it (rows ascending, first strictly smaller wins: the packed order) is
-// folded into the bin of j's component; the bins become row A of P, whose
-// symmetrization and column minima follow as for a stored W.
-constexpr u32 CP_THREADS = 512;
-
-template <int DT, int D>
-__global__ void __launch_bounds__(CP_THREADS, 1) k_contract_pts(ContractArgs a, const float* __restrict__ P)
-{
-    constexpr int CPC = cols_per_thread<D>();
-    extern __shared__ __align__(16) u64 bins[];
-    __shared__ __align__(16) float s_rp[CONTRACT_ROWS * D];
-    __shared__ u32 s_item, s_rows[CONTRACT_ROWS];
-    __shared__ u64 s_red[32];
-    Counters* ctr = a.ctr;
-    if (*(volatile u32*)&ctr->done)
-        return;
-    const u32 cr = ((volatile u32*)ctr->c)[0];   // level 0: n
-    const u32 cn = ((volatile u32*)ctr->c)[1];
-    const u32 tid = threadIdx.x, bd = blockDim.x;
-    if (cr <= a.comp_max_c)
-        for (u32 v = blockIdx.x * bd + tid; v < a.n; v += gridDim.x * bd)
-            a.comp[v] = a.label[a.comp[v]];
-    const u32 total_chunks = *(volatile u32*)&ctr->total_chunks;
-    const u32 nbr = (cn + a.bin_cap - 1) / a.bin_cap;
-    const u32 total = total_chunks * nbr;
-    for (;;) {
-        if (tid == 0)
-            s_item = atomicAdd(&ctr->item_next, 1u);
-        __syncthreads();
-        const u32 item = s_item;
-        if (item >= total)
-            break;
-        const u32 br = item / total_chunks, ch = item - br * total_chunks;
-        const u32 A = a.item_group[ch];
-        const u32 kq = ch - a.chunk_start[A];
-        const u32 m0 = a.gstart[A] + kq * CONTRACT_ROWS;
-        const u32 m1 = min(a.gstart[A + 1], m0 + CONTRACT_ROWS);
-        const u32 nrows = m1 - m0;
-        const bool single = a.nchunk[A] == 1;
-        const u32 b0 = br * a.bin_cap;
-        const u32 nb = min(cn - b0, a.bin_cap);
-        if (tid < nrows)
-            s_rows[tid] = a.members[m0 + tid];
-        for (u32 b = tid; b < nb; b += bd)
-            bins[b] = EDGE_INF;
-        __syncthreads();
-        if (tid == 0) {   // rows ascending (at most CONTRACT_ROWS)
-            for (u32 q = 1; q < nrows; ++q) {
-                const u32 v = s_rows[q];
-                u32 p = q;
-                while (p > 0 && s_rows[p - 1] > v) {
-                    s_rows[p] = s_rows[p - 1];
-                    --p;
-                }
-                s_rows[p] = v;
-            }
-        }
-        __syncthreads();
-        for (u32 e = tid; e < nrows * D; e += bd)
-            s_rp[e] = P[(size_t)s_rows[e / D] * D + (e % D)];
-        __syncthreads();
-        const u32 r0 = s_rows[0];
-        for (u32 g = (r0 + 1) / CPC + tid; g * CPC < cr; g += bd) {
-            const u32 j = g * CPC;
-            float cx[CPC][D];
-#pragma unroll
-            for (int c = 0; c < CPC; ++c)
-                load_pt<D>(P + (size_t)(j + c) * D, cx[c]);
-            u32 bk[CPC], bi[CPC];
-#pragma unroll
-            for (int c = 0; c < CPC; ++c)
-                bk[c] = bi[c] = 0xFFFFFFFFu;
-            for (u32 q = 0; q < nrows; ++q) {
-                const u32 row = s_rows[q];
-                if (row >= j + CPC - 1)   // rows ascending: none of the rest reach these columns
-                    break;
-                float rx[D];
-#pragma unroll
-                for (int k = 0; k < D; ++k)
-                    rx[k] = s_rp[q * D + k];
-#pragma unroll
-                for (int c = 0; c < CPC; ++c) {
-                    const u32 k = key_of(__float_as_uint(sq_dist<D>(rx, cx[c])), DT);
-                    if (j + c > row && (bi[c] == 0xFFFFFFFFu || k < bk[c])) {
-                        bk[c] = k;
-                        bi[c] = row;
-                    }
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CPC; ++c) {
-                const u32 col = j + c;
-                if (bi[c] == 0xFFFFFFFFu || col >= cr)
-                    continue;
-                const u32 L = a.label[col];
-                const u32 rel = L - b0;
-                if (L == A || rel >= nb)
-                    continue;
-                const u64 e = ((u64)bk[c] << 32) | pair_code(bi[c], col, cr);
-                if (e < bins[rel])
-                    atomicMin(&bins[rel], e);
-            }
-        }
-        __syncthreads();
-        // row A of P (this bin range) and its minimum
-        u64 m = EDGE_INF;
-        u64* dst = a.cout + (size_t)A * cn + b0;
-        for (u32 b = tid; b < nb; b += bd) {
-            const u64 v = bins[b];
-            if (single)
-                dst[b] = v;
-            else if (v != EDGE_INF)
-                atomicMin(dst + b, v);
-            m = v < m ? v : m;
-        }
-        m = block_min_u64(m, s_red);
-        if (tid == 0 && m != EDGE_INF)
-            atomicMin(&a.best_out[A], m);
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------ level 0, sorted columns
 // After the level-0 step the members list holds the vertices grouped by
 // component (group A at positions gstart[A] .. gstart[A+1]).  k_pts_gather
 // copies the coordinates into that order (Ps), with each position's vertex
-// (pvid) and component (pcomp).  k_contract_pts_sorted then takes group A's
-// rows against every later position: those columns belong to groups B > A,
-// each group's columns contiguous, so P'(A, B) = min over the run of B's
-// columns of the column minima -- a run reduction instead of a bin array.
-// Row A of P' holds INF for B <= A, so C_1(A, B) = min(P'(A, B), P'(B, A))
-// as for the upper-triangle P of a stored W, and the same column minima and
-// level-1 symmetrization follow.
+// (pvid) and component (pcomp).  k_contract_pts_sorted then takes a chunk of
+// at most CONTRACT_ROWS rows of a group A (the step's work items, so a large
+// group is shared by several CTAs) against every later position: those
+// columns belong to groups B > A, each group's columns contiguous, so
+// P'(A, B) = min over the run of B's columns of the column minima -- a run
+// reduction instead of a bin array.  Row A of P' holds INF for B <= A (the
+// step leaves a group of several chunks an all-INF row, and its chunks merge
+// by atomic minima), so C_1(A, B) = min(P'(A, B), P'(B, A)) as for the
+// upper-triangle P of a stored W, and the same column minima and level-1
+// symmetrization follow.
 __global__ void k_pts_gather(const float* __restrict__ P, int D, const u32* __restrict__ members,
                              const u32* __restrict__ label, u32 n, float* __restrict__ Ps,
                              u32* __restrict__ pvid, u32* __restrict__ pcomp)
@@ -357,7 +225,6 @@ __global__ void k_pts_gather(const float* __restrict__ P, int D, const u32* __re
 }
 
 constexpr u32 CS_THREADS = 256;
-constexpr u32 CS_ROWCAP = 256;   // rows of a group kept in shared memory
 
 template <int D>
 constexpr int cols_sorted()
@@ -370,10 +237,11 @@ __global__ void __launch_bounds__(CS_THREADS, 3)
     k_contract_pts_sorted(ContractArgs a, const float* __restrict__ Ps, const u32* __restrict__ pvid,
                           const u32* __restrict__ pcomp)
 {
-    constexpr int CPC = cols_sorted<D>();
-    constexpr u32 CH = CS_THREADS * CPC;   // columns per chunk
-    __shared__ __align__(16) float s_rp[CS_ROWCAP * D];
-    __shared__ u32 s_rv[CS_ROWCAP];
+    constexpr int CPC = cols_sorted<D>();       // columns per thread and pass
+    constexpr int PASSES = 8 / CPC;             // passes per chunk between barriers
+    constexpr u32 CH = CS_THREADS * CPC * PASSES;   // columns per chunk (2048)
+    __shared__ __align__(16) float s_rp[CONTRACT_ROWS * D];
+    __shared__ u32 s_rv[CONTRACT_ROWS];
     __shared__ u64 s_e[CH];
     __shared__ u32 s_b[CH];
     __shared__ u32 s_item;
@@ -385,6 +253,7 @@ __global__ void __launch_bounds__(CS_THREADS, 3)
         return;
     const u32 n = ((volatile u32*)ctr->c)[0];
     const u32 cn = ((volatile u32*)ctr->c)[1];
+    const u32 total_chunks = *(volatile u32*)&ctr->total_chunks;
     const u32 tid = threadIdx.x;
     if (n <= a.comp_max_c)
         for (u32 v = blockIdx.x * blockDim.x + tid; v < a.n; v += gridDim.x * blockDim.x)
@@ -393,79 +262,86 @@ __global__ void __launch_bounds__(CS_THREADS, 3)
         if (tid == 0)
             s_item = atomicAdd(&ctr->item_next, 1u);
         __syncthreads();
-        const u32 A = s_item;
-        if (A >= cn)
+        const u32 ch = s_item;
+        if (ch >= total_chunks)
             break;
-        const u32 g0 = a.gstart[A], g1 = a.gstart[A + 1];
-        const u32 nrows = g1 - g0;
-        const bool rows_in_smem = nrows <= CS_ROWCAP;
-        if (rows_in_smem) {
-            for (u32 e = tid; e < nrows * D; e += CS_THREADS)
-                s_rp[e] = Ps[(size_t)g0 * D + e];
-            for (u32 r = tid; r < nrows; r += CS_THREADS)
-                s_rv[r] = pvid[g0 + r];
-        }
+        const u32 A = a.item_group[ch];
+        const u32 g0 = a.gstart[A] + (ch - a.chunk_start[A]) * CONTRACT_ROWS;
+        const u32 nrows = min(a.gstart[A + 1], g0 + CONTRACT_ROWS) - g0;
+        const bool single = a.nchunk[A] == 1;
+        const u32 qbeg = a.gstart[A + 1];   // the first position of a later group
+        for (u32 e = tid; e < nrows * D; e += CS_THREADS)
+            s_rp[e] = Ps[(size_t)g0 * D + e];
+        if (tid < nrows)
+            s_rv[tid] = pvid[g0 + tid];
         u64* row = a.cout + (size_t)A * cn;
-        for (u32 b = tid; b <= A; b += CS_THREADS)   // no pairs with groups B <= A
-            row[b] = EDGE_INF;
+        if (single)   // no pairs with groups B <= A (a multi-chunk row is all INF already)
+            for (u32 b = tid; b <= A; b += CS_THREADS)
+                row[b] = EDGE_INF;
         if (tid == 0) {
             s_carry_b[0] = 0xFFFFFFFFu;
             s_carry_e[0] = EDGE_INF;
         }
-        u64 mrow = EDGE_INF;   // this thread's part of row A's minimum
+        u64 mrow = EDGE_INF;   // this thread's part of the chunk's row minimum
+        auto put = [&](u32 B, u64 v) {
+            if (single)
+                row[B] = v;
+            else if (v < row[B])
+                atomicMin(row + B, v);
+            mrow = v < mrow ? v : mrow;
+        };
         __syncthreads();
         int cur = 0;
-        for (u32 q0 = g1; q0 < n; q0 += CH) {
-            // 1. each column's smallest (key, row vertex) over the group's rows
-            const u32 qt = q0 + tid * CPC;
-            float cx[CPC][D];
-            u32 bk[CPC], bv[CPC], vq[CPC];
+        for (u32 q0 = qbeg; q0 < n; q0 += CH) {
+            // 1. each column's smallest (order, row vertex) over the chunk's
+            // rows; in pass p thread t takes the columns
+            // q0 + t + (p * CPC + c) * CS_THREADS, so the coordinate loads and
+            // the shared-memory stores run contiguously across a warp
+#pragma unroll 1
+            for (int pass = 0; pass < PASSES; ++pass) {
+                float cx[CPC][D];
+                u32 bk[CPC], bv[CPC], vq[CPC];
 #pragma unroll
-            for (int c = 0; c < CPC; ++c) {
-                const u32 q = qt + c;
-                if (q < n) {
-                    load_pt<D>(Ps + (size_t)q * D, cx[c]);
-                    vq[c] = pvid[q];
-                } else {
+                for (int c = 0; c < CPC; ++c) {
+                    const u32 q = q0 + tid + (pass * CPC + c) * CS_THREADS;
+                    if (q < n) {
+                        load_pt<D>(Ps + (size_t)q * D, cx[c]);
+                        vq[c] = pvid[q];
+                    } else {
 #pragma unroll
-                    for (int k = 0; k < D; ++k)
-                        cx[c][k] = 0.0f;
-                    vq[c] = 0u;
+                        for (int k = 0; k < D; ++k)
+                            cx[c][k] = 0.0f;
+                        vq[c] = 0u;
+                    }
+                    bk[c] = bv[c] = 0xFFFFFFFFu;
                 }
-                bk[c] = bv[c] = 0xFFFFFFFFu;
-            }
-            for (u32 r = 0; r < nrows; ++r) {
-                float rx[D];
-                u32 vr;
-                if (rows_in_smem) {
+                for (u32 r = 0; r < nrows; ++r) {
+                    float rx[D];
 #pragma unroll
                     for (int k = 0; k < D; ++k)
                         rx[k] = s_rp[r * D + k];
-                    vr = s_rv[r];
-                } else {
-                    load_pt<D>(Ps + (size_t)(g0 + r) * D, rx);
-                    vr = pvid[g0 + r];
+                    const u32 vr = s_rv[r];
+#pragma unroll
+                    for (int c = 0; c < CPC; ++c) {
+                        const u32 u = sbits_order<DT>(sq_dist<D>(rx, cx[c]));
+                        if (u < bk[c] || (u == bk[c] && vr < bv[c])) {
+                            bk[c] = u;
+                            bv[c] = vr;
+                        }
+                    }
                 }
 #pragma unroll
                 for (int c = 0; c < CPC; ++c) {
-                    const u32 u = sbits_order<DT>(sq_dist<D>(rx, cx[c]));
-                    if (u < bk[c] || (u == bk[c] && vr < bv[c])) {
-                        bk[c] = u;
-                        bv[c] = vr;
+                    const u32 i = tid + (pass * CPC + c) * CS_THREADS;
+                    const u32 q = q0 + i;
+                    if (q < n && bv[c] != 0xFFFFFFFFu) {
+                        s_e[i] = ((u64)order_to_key<DT>(bk[c]) << 32) |
+                                 pair_code(min(bv[c], vq[c]), max(bv[c], vq[c]), n);
+                        s_b[i] = pcomp[q];
+                    } else {
+                        s_e[i] = EDGE_INF;
+                        s_b[i] = q < n ? pcomp[q] : 0xFFFFFFFFu;
                     }
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CPC; ++c) {
-                const u32 q = qt + c;
-                const u32 i = tid * CPC + c;
-                if (q < n && bv[c] != 0xFFFFFFFFu) {
-                    s_e[i] = ((u64)order_to_key<DT>(bk[c]) << 32) |
-                             pair_code(min(bv[c], vq[c]), max(bv[c], vq[c]), n);
-                    s_b[i] = pcomp[q];
-                } else {
-                    s_e[i] = EDGE_INF;
-                    s_b[i] = q < n ? pcomp[q] : 0xFFFFFFFFu;
                 }
             }
             __syncthreads();
@@ -483,16 +359,13 @@ __global__ void __launch_bounds__(CS_THREADS, 3)
                 for (; j < ncol && s_b[j] == B; ++j)
                     v = s_e[j] < v ? s_e[j] : v;
                 if (i == 0) {
-                    if (cb == B) {
+                    if (cb == B)
                         v = ce < v ? ce : v;
-                    } else if (cb != 0xFFFFFFFFu) {
-                        row[cb] = ce;   // the carried run ended with the last chunk
-                        mrow = ce < mrow ? ce : mrow;
-                    }
+                    else if (cb != 0xFFFFFFFFu)
+                        put(cb, ce);   // the carried run ended with the last chunk
                 }
                 if (j < ncol) {
-                    row[B] = v;
-                    mrow = v < mrow ? v : mrow;
+                    put(B, v);
                 } else {
                     s_carry_b[cur ^ 1] = B;
                     s_carry_e[cur ^ 1] = v;
@@ -501,12 +374,9 @@ __global__ void __launch_bounds__(CS_THREADS, 3)
             cur ^= 1;
             __syncthreads();
         }
-        // the last run of the item
-        if (tid == 0 && s_carry_b[cur] != 0xFFFFFFFFu) {
-            const u64 v = s_carry_e[cur];
-            row[s_carry_b[cur]] = v;
-            mrow = v < mrow ? v : mrow;
-        }
+        // the last run of the chunk's columns
+        if (tid == 0 && s_carry_b[cur] != 0xFFFFFFFFu)
+            put(s_carry_b[cur], s_carry_e[cur]);
         mrow = block_min_u64(mrow, s_red);
         if (tid == 0 && mrow != EDGE_INF)
             atomicMin(&a.best_out[A], mrow);
@@ -586,45 +456,6 @@ cudaError_t launch_rowmin_pts(const float* P, int D, u32 n, int dt, u64* best, c
     return (dt & 2) ? rowmin_pts_dt<2>(P, D, n, best, s) : rowmin_pts_dt<0>(P, D, n, best, s);
 }
 
-template <int DT, int D>
-static cudaError_t contract_pts_d(const ContractArgs& ca, const float* P, int blocks, size_t smem,
-                                  cudaStream_t s)
-{
-    auto k = k_contract_pts<DT, D>;
-    cudaError_t e = set_smem_pts(k, smem);
-    if (e != cudaSuccess)
-        return e;
-    k<<<blocks, CP_THREADS, smem, s>>>(ca, P);
-    return cudaGetLastError();
-}
-
-template <int DT>
-static cudaError_t contract_pts_dt(const ContractArgs& ca, const float* P, int D, int blocks, size_t smem,
-                                   cudaStream_t s)
-{
-    switch (D) {
-    case 2: return contract_pts_d<DT, 2>(ca, P, blocks, smem, s);
-    case 4: return contract_pts_d<DT, 4>(ca, P, blocks, smem, s);
-    case 8: return contract_pts_d<DT, 8>(ca, P, blocks, smem, s);
-    case 16: return contract_pts_d<DT, 16>(ca, P, blocks, smem, s);
-    default: return contract_pts_d<DT, 32>(ca, P, blocks, smem, s);
-    }
-}
-
-// one CTA per SM with every bin the shared memory holds (a second bin range
-// would compute every distance again)
-u32 contract_pts_bin_cap(int smem_optin)
-{
-    return (u32)((smem_optin - 4096) / 8);
-}
-
-cudaError_t launch_contract_pts(const ContractArgs& ca, const float* P, int D, int dt, int blocks,
-                                cudaStream_t s)
-{
-    const size_t smem = (size_t)ca.bin_cap * sizeof(u64);
-    return (dt & 2) ? contract_pts_dt<2>(ca, P, D, blocks, smem, s) : contract_pts_dt<0>(ca, P, D, blocks, smem, s);
-}
-
 cudaError_t launch_pts_gather(const float* P, int D, const u32* members, const u32* label, u32 n, float* Ps,
                               u32* pvid, u32* pcomp, cudaStream_t s)
 {
@@ -670,10 +501,7 @@ cudaError_t preload_points()
 {
     return touch_kernels(k_pts_pad, k_rowmin_pts<0, 2>, k_rowmin_pts<0, 4>, k_rowmin_pts<0, 8>,
                          k_rowmin_pts<0, 16>, k_rowmin_pts<0, 32>, k_rowmin_pts<2, 2>, k_rowmin_pts<2, 4>,
-                         k_rowmin_pts<2, 8>, k_rowmin_pts<2, 16>, k_rowmin_pts<2, 32>, k_contract_pts<0, 2>,
-                         k_contract_pts<0, 4>, k_contract_pts<0, 8>, k_contract_pts<0, 16>,
-                         k_contract_pts<0, 32>, k_contract_pts<2, 2>, k_contract_pts<2, 4>,
-                         k_contract_pts<2, 8>, k_contract_pts<2, 16>, k_contract_pts<2, 32>, k_mst_sqrt<0>,
+                         k_rowmin_pts<2, 8>, k_rowmin_pts<2, 16>, k_rowmin_pts<2, 32>, k_mst_sqrt<0>,
                          k_mst_sqrt<2>, k_pts_gather, k_contract_pts_sorted<0, 2>, k_contract_pts_sorted<0, 4>,
                          k_contract_pts_sorted<0, 8>, k_contract_pts_sorted<0, 16>,
                          k_contract_pts_sorted<0, 32>, k_contract_pts_sorted<2, 2>,

@@ -203,6 +203,9 @@ appd_status appd_server_create(size_t budget_bytes, int32_t max_inflight, appd_s
         return APPD_ERR_CUDA;
     }
     sv->status = device_status_word();
+    // the batched path's parameters as they are set for this process
+    // (appd_batched_tuning, appd_batched_prim_max or appd_batched_autotune)
+    sv->tune = current_batch_tuning();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
     }

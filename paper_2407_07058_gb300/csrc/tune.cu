@@ -1,13 +1,15 @@
 // tune.cu -- autotuner of the batched path.
 //
-// The batched path has two shape parameters that depend on the GPU: the rows
-// per fill batch inside a CTA (shared memory per CTA vs. the number of row
-// batches per column block) and the size cut-over between one-CTA-per-graph
-// solving and the multi-CTA pipeline.  appd_batched_autotune times every candidate
-// pair on a seeded synthetic batch (graph sizes log-uniform in [32, 4096],
-// uniform(0,1) weights written by a hash kernel below), keeps the fastest,
-// installs it for this process, and caches it in a small JSON file keyed by
-// the GPU name and driver version so later processes skip the search.
+// The batched path has three shape parameters that depend on the GPU: the
+// rows per fill batch inside a CTA (shared memory per CTA vs. the number of
+// row batches per column block), the size cut-over between one-CTA-per-graph
+// solving and the multi-CTA pipeline, and the largest graph one warp solves
+// by Prim.  appd_batched_autotune times every (fill rows, cut-over) pair, then
+// every warp limit with the best pair, on a seeded synthetic batch (graph sizes
+// log-uniform in [32, 4096], uniform(0,1) weights written by a hash kernel
+// below), keeps the fastest, installs it for this process, and caches it in a
+// small JSON file keyed by the GPU name and driver version so later processes
+// skip the search.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -63,7 +65,8 @@ bool cache_key(std::string* key)
     return true;
 }
 
-// The cache file holds one line per key:  {"key": "...", "fill_rows": R, "n_split": S}
+// The cache file holds one line per key:
+//   {"key": "...", "fill_rows": R, "n_split": S, "prim_max": P}
 bool cache_lookup(const char* path, const std::string& key, BatchTuning* out)
 {
     FILE* f = fopen(path, "r");
@@ -80,10 +83,15 @@ bool cache_lookup(const char* path, const std::string& key, BatchTuning* out)
         const size_t a = l.find("\"fill_rows\": "), b = l.find("\"n_split\": ");
         if (a == std::string::npos || b == std::string::npos)
             continue;
+        const size_t c = l.find("\"prim_max\": ");
+        int pm = 0;
+        if (c == std::string::npos || sscanf(l.c_str() + c + 12, "%d", &pm) != 1)
+            continue;   // an entry written before the warp limit was searched
         if (sscanf(l.c_str() + a + 13, "%d", &fr) == 1 && sscanf(l.c_str() + b + 11, "%lld", &ns) == 1) {
             out->fill_rows = fr;
             out->n_split = ns;
             out->ctas_per_sm = 1;
+            out->prim_max = (u32)pm;
             found = true;
         }
     }
@@ -96,8 +104,8 @@ void cache_store(const char* path, const std::string& key, const BatchTuning& t,
     FILE* f = fopen(path, "a");
     if (!f)
         return;
-    fprintf(f, "{\"key\": \"%s\", \"fill_rows\": %d, \"n_split\": %lld, \"ms\": %.4f}\n", key.c_str(),
-            t.fill_rows, (long long)t.n_split, ms);
+    fprintf(f, "{\"key\": \"%s\", \"fill_rows\": %d, \"n_split\": %lld, \"prim_max\": %u, \"ms\": %.4f}\n",
+            key.c_str(), t.fill_rows, (long long)t.n_split, t.prim_max, ms);
     fclose(f);
 }
 
@@ -112,8 +120,10 @@ extern "C" appd_status appd_batched_autotune(const char* cache_path, appd_stream
     if (!cache_key(&key))
         return APPD_ERR_CUDA;
     BatchTuning best;
-    if (cache_path && cache_lookup(cache_path, key, &best))
-        return appd_batched_tuning(best.ctas_per_sm, best.fill_rows, best.n_split);
+    if (cache_path && cache_lookup(cache_path, key, &best)) {
+        appd_status st = appd_batched_tuning(best.ctas_per_sm, best.fill_rows, best.n_split);
+        return st == APPD_OK ? appd_batched_prim_max((int32_t)best.prim_max) : st;
+    }
     cudaStream_t cs = (cudaStream_t)s;
     // synthetic batch: 192 graphs, n = floor(32 * 128^u), u from a fixed sequence
     const int G = 192;
@@ -143,23 +153,29 @@ extern "C" appd_status appd_batched_autotune(const char* cache_path, appd_stream
     cudaEventCreate(&e1);
     const int rows[] = {256, 512, 1024, 2048};
     const int64_t splits[] = {512, 1024, 2048, 4096};
+    const int prims[] = {0, 64, 128, 256, 512};
     double best_ms = 1e30;
     appd_status st = APPD_OK;
+    // times the current parameters: a warm-up call (builds the runtime and
+    // the captured launch), then one timed call
+    auto time_batch = [&](float* ms) -> appd_status {
+        appd_status r = appd_solve_batched(offs.data(), W, ns.data(), nullptr, M, G, s);
+        if (r != APPD_OK)
+            return r;
+        cudaEventRecord(e0, cs);
+        r = appd_solve_batched(offs.data(), W, ns.data(), nullptr, M, G, s);
+        cudaEventRecord(e1, cs);
+        if (r != APPD_OK || cudaEventSynchronize(e1) != cudaSuccess)
+            return r != APPD_OK ? r : APPD_ERR_CUDA;
+        cudaEventElapsedTime(ms, e0, e1);
+        return APPD_OK;
+    };
+    best.prim_max = current_batch_tuning().prim_max;
     for (int r : rows) {
         for (int64_t sp : splits) {
-            if ((st = appd_batched_tuning(1, r, sp)) != APPD_OK)
-                break;
-            // warm-up (builds the runtime and the captured launch), then time
-            st = appd_solve_batched(offs.data(), W, ns.data(), nullptr, M, G, s);
-            if (st != APPD_OK)
-                break;
-            cudaEventRecord(e0, cs);
-            st = appd_solve_batched(offs.data(), W, ns.data(), nullptr, M, G, s);
-            cudaEventRecord(e1, cs);
-            if (st != APPD_OK || cudaEventSynchronize(e1) != cudaSuccess)
-                break;
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            if ((st = appd_batched_tuning(1, r, sp)) != APPD_OK || (st = time_batch(&ms)) != APPD_OK)
+                break;
             if (ms < best_ms) {
                 best_ms = ms;
                 best.ctas_per_sm = 1;
@@ -170,6 +186,17 @@ extern "C" appd_status appd_batched_autotune(const char* cache_path, appd_stream
         if (st != APPD_OK)
             break;
     }
+    if (st == APPD_OK && (st = appd_batched_tuning(1, best.fill_rows, best.n_split)) == APPD_OK) {
+        for (int pm : prims) {
+            float ms = 0.f;
+            if ((st = appd_batched_prim_max(pm)) != APPD_OK || (st = time_batch(&ms)) != APPD_OK)
+                break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.prim_max = (u32)pm;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(cs);
@@ -179,7 +206,8 @@ extern "C" appd_status appd_batched_autotune(const char* cache_path, appd_stream
         return st;
     if (cache_path)
         cache_store(cache_path, key, best, best_ms);
-    return appd_batched_tuning(best.ctas_per_sm, best.fill_rows, best.n_split);
+    st = appd_batched_tuning(best.ctas_per_sm, best.fill_rows, best.n_split);
+    return st == APPD_OK ? appd_batched_prim_max((int32_t)best.prim_max) : st;
 }
 
 extern "C" appd_status appd_batched_get_tuning(int32_t* ctas_per_sm, int32_t* fill_rows, int64_t* n_split)

@@ -62,11 +62,17 @@ def test_argument_errors_need_no_gpu():
 
 def test_tuning_readback_needs_no_gpu():
     appd.batched_tuning(1, 128, 1024)
+    appd.batched_prim_max(64)
     try:
-        assert appd.get_batched_tuning() == {"ctas_per_sm": 1, "fill_rows": 128, "n_split": 1024}
+        assert appd.get_batched_tuning() == {"ctas_per_sm": 1, "fill_rows": 128, "n_split": 1024,
+                                             "prim_max": 64}
     finally:
         appd.batched_tuning()
-    assert appd.get_batched_tuning() == {"ctas_per_sm": 1, "fill_rows": 256, "n_split": 2048}
+        appd.batched_prim_max()
+    assert appd.get_batched_tuning() == {"ctas_per_sm": 1, "fill_rows": 256, "n_split": 2048,
+                                         "prim_max": 256}
+    lib = appd.load()
+    assert lib.appd_batched_prim_max(513) == 1 and lib.appd_batched_prim_max(-1) == 1
 
 
 def test_build_is_in_tree_for_sm103a():
