@@ -601,43 +601,52 @@ def one_by_one(inp, idx, dev):
 
 
 def bench_serving(dev, count: int = 20000):
-    """Continuous batching under a 40 GB budget: capacity at saturation, the
-    same requests one at a time, then Poisson arrivals at 0.5x and 0.8x of
-    the capacity; graphs/s and p50/p99 latency."""
+    """Continuous batching under a 40 GB budget, at two size cut-overs of the
+    server's batched path: graphs up to 2048 vertices one per CTA and larger
+    ones on the whole GPU (latency-oriented), or every graph of the mix one per
+    CTA (capacity-oriented).  For each: capacity at saturation and Poisson
+    arrivals at fractions of it (graphs/s, p50/p99 latency); the same
+    requests one at a time with plain solves for comparison."""
     from paper_2407_07058_gb300 import appd
     budget = 40 << 30
     ns, dts = serving_requests(count)
     inp = ServingInputs(ns, dts, dev)
-    sv = appd.Server(budget, 8192)
+    m = min(count, 4000)
+    wall1, dev1 = one_by_one(inp, np.arange(m), dev)
+    base = appd.get_batched_tuning()
+    out = {"workload": f"{count} requests, n log-uniform in [64, 8192), half FP32 2-D "
+                       "mixture distances (FP32 arithmetic), half uint32 uniform [0, 2^16); "
+                       "40 GB budget",
+           "capacity_requests": m,
+           "one_by_one_graphs_per_s": m / wall1,
+           "one_by_one_device_graphs_per_s": m / dev1}
+    rng = np.random.default_rng(55)
     try:
-        # warm-up, then capacity: a saturating burst (all arrive at t = 0)
-        run_serving(sv, inp, np.arange(300), np.zeros(300), dev)
-        m = min(count, 4000)
-        _, _, wall = run_serving(sv, inp, np.arange(m), np.zeros(m), dev)
-        cap = m / wall
-        wall1, dev1 = one_by_one(inp, np.arange(m), dev)
-        out = {"workload": f"{count} requests, n log-uniform in [64, 8192], half FP32 2-D "
-                           "mixture distances (FP32 arithmetic), half uint32 uniform [0, 2^16); "
-                           "40 GB budget",
-               "capacity_graphs_per_s": cap,
-               "capacity_requests": m,
-               "one_by_one_graphs_per_s": m / wall1,
-               "one_by_one_device_graphs_per_s": m / dev1,
-               "served_vs_one_by_one": cap / (m / wall1),
-               "rates": []}
-        rng = np.random.default_rng(55)
-        for frac in (0.5, 0.8):
-            lam = frac * cap
-            arr = np.cumsum(rng.exponential(1.0 / lam, size=count))
-            lat, ing, wall = run_serving(sv, inp, np.arange(count), arr, dev)
-            out["rates"].append({"rate_frac_of_capacity": frac, "rate_per_s": lam,
-                                 "graphs_per_s": count / wall,
-                                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                                 "max_ms": 1e3 * float(lat.max()),
-                                 "ingress_host_p50_ms": 1e3 * float(np.percentile(ing, 50))})
+        for mode, n_split, fracs in (("latency_mode", 2048, (0.5, 0.8)), ("capacity_mode", 8192, (0.5,))):
+            appd.batched_tuning(base["ctas_per_sm"], base["fill_rows"], n_split)
+            sv = appd.Server(budget, 8192)
+            try:
+                # warm-up, then capacity: a saturating burst (all arrive at t = 0)
+                run_serving(sv, inp, np.arange(300), np.zeros(300), dev)
+                _, _, wall = run_serving(sv, inp, np.arange(m), np.zeros(m), dev)
+                cap = m / wall
+                res = {"n_split": n_split, "capacity_graphs_per_s": cap,
+                       "served_vs_one_by_one": cap / (m / wall1), "rates": []}
+                for frac in fracs:
+                    lam = frac * cap
+                    arr = np.cumsum(rng.exponential(1.0 / lam, size=count))
+                    lat, ing, wall = run_serving(sv, inp, np.arange(count), arr, dev)
+                    res["rates"].append({"rate_frac_of_capacity": frac, "rate_per_s": lam,
+                                         "graphs_per_s": count / wall,
+                                         "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                                         "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                                         "max_ms": 1e3 * float(lat.max()),
+                                         "ingress_host_p50_ms": 1e3 * float(np.percentile(ing, 50))})
+                out[mode] = res
+            finally:
+                sv.close()
     finally:
-        sv.close()
+        appd.batched_tuning(base["ctas_per_sm"], base["fill_rows"], base["n_split"])
     return out
 
 
