@@ -40,6 +40,37 @@ __device__ __forceinline__ float sq_dist(const float (&a)[D], const float (&b)[D
     return s;
 }
 
+// Two columns' squared distances to one row at once with the packed FP32
+// instructions (sub.rn.f32x2, fma.rn.f32x2: each half rounded exactly as the
+// scalar __fsub_rn / __fmaf_rn, so the sums are bit-identical to sq_dist):
+// rr[k] holds the row's coordinate k in both halves, c2[k] the two columns'
+// coordinates k (low half: the first column).  Half the issue slots of two
+// scalar sums; the FMA pipe's throughput is the same.
+template <int D>
+__device__ __forceinline__ u64 sq_dist2(const u64* rr, const u64 (&c2)[D])
+{
+    u64 s = 0ull;   // +0.0f in both halves
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        u64 t;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(rr[k]), "l"(c2[k]));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(s) : "l"(t));
+    }
+    return s;
+}
+
+__device__ __forceinline__ u64 pack_f2(float lo, float hi)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack_f2(u64 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 template <int D>
 __device__ __forceinline__ void load_pt(const float* __restrict__ p, float (&x)[D])
 {
@@ -107,13 +138,21 @@ __global__ void k_pts_pad(const float* __restrict__ X, u32 n, int d, int D, u32 
 // smallest key at the smallest row (and, per row, the smallest column).
 constexpr u32 RP_ROWS = 256, RP_THREADS = 256;
 
+// For D <= 16 the columns are taken in pairs with the packed FP32
+// instructions (sq_dist2), the rows' coordinates stored twice per word in
+// shared memory; D = 32 keeps scalar sums (its doubled rows would not fit
+// the static shared memory).
 template <int DT, int D>
 __global__ void __launch_bounds__(RP_THREADS, 2)
     k_rowmin_pts(const float* __restrict__ P, u32 n, u64* __restrict__ best)
 {
     constexpr int CPL = cols_per_lane<D>();
+    constexpr bool PACKED = D <= 16;
     constexpr u32 TCOLS = 8 * 32 * CPL;
-    __shared__ __align__(16) float s_pts[RP_ROWS * D];
+    constexpr int SW = PACKED ? RP_ROWS * D : 1;   // packed row words
+    constexpr int SF = PACKED ? 1 : RP_ROWS * D;   // scalar row words
+    __shared__ __align__(16) u64 s_pts2[SW];
+    __shared__ __align__(16) float s_pts[SF];
     __shared__ u64 s_row[RP_ROWS];
     const u32 i0 = blockIdx.y * RP_ROWS, c0 = blockIdx.x * TCOLS;
     if (c0 + TCOLS - 1 <= i0 || i0 >= n || c0 >= n)   // no pair i < j in this tile
@@ -122,8 +161,13 @@ __global__ void __launch_bounds__(RP_THREADS, 2)
     const u32 imax = min(n, i0 + RP_ROWS);
     for (u32 r = threadIdx.x; r < RP_ROWS; r += blockDim.x)
         s_row[r] = EDGE_INF;
-    for (u32 e = threadIdx.x; e < RP_ROWS * D; e += blockDim.x)
-        s_pts[e] = P[(size_t)i0 * D + e];   // P has npad >= i0 + RP_ROWS rows
+    for (u32 e = threadIdx.x; e < RP_ROWS * D; e += blockDim.x) {
+        const float x = P[(size_t)i0 * D + e];   // P has npad >= i0 + RP_ROWS rows
+        if constexpr (PACKED)
+            s_pts2[e] = pack_f2(x, x);
+        else
+            s_pts[e] = x;
+    }
     __syncthreads();
     const u32 j = c0 + (32 * w + lane) * CPL;   // this lane's first column
     float cx[CPL][D];
@@ -137,6 +181,14 @@ __global__ void __launch_bounds__(RP_THREADS, 2)
                 cx[c][k] = 0.0f;
         }
     }
+    u64 cx2[CPL / 2][PACKED ? D : 1];
+    if constexpr (PACKED) {
+#pragma unroll
+        for (int p2 = 0; p2 < CPL / 2; ++p2)
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                cx2[p2][k] = pack_f2(cx[2 * p2][k], cx[2 * p2 + 1][k]);
+    }
     u32 ck[CPL], ci[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c)
@@ -146,15 +198,27 @@ __global__ void __launch_bounds__(RP_THREADS, 2)
     const bool clear = c0 >= imax && c0 + TCOLS <= n;
     // (the order values below are the keys' order; see sbits_order)
     for (u32 i = imax; i-- > i0;) {
-        float rx[D];
+        // the row's squared distances to this lane's columns
+        float sd[CPL];
+        if constexpr (PACKED) {
+            const u64* rr = s_pts2 + (size_t)(i - i0) * D;
 #pragma unroll
-        for (int k = 0; k < D; ++k)
-            rx[k] = s_pts[(i - i0) * D + k];
+            for (int p2 = 0; p2 < CPL / 2; ++p2)
+                unpack_f2(sq_dist2<D>(rr, cx2[p2]), sd[2 * p2], sd[2 * p2 + 1]);
+        } else {
+            float rx[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                rx[k] = s_pts[(i - i0) * D + k];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+                sd[c] = sq_dist<D>(rx, cx[c]);
+        }
         u32 rk = 0xFFFFFFFFu, rj = 0xFFFFFFFFu;
         if (clear) {
 #pragma unroll
             for (int c = CPL - 1; c >= 0; --c) {
-                const u32 u = sbits_order<DT>(sq_dist<D>(rx, cx[c]));
+                const u32 u = sbits_order<DT>(sd[c]);
                 if (u <= rk) {
                     rk = u;
                     rj = j + c;
@@ -168,7 +232,7 @@ __global__ void __launch_bounds__(RP_THREADS, 2)
 #pragma unroll
             for (int c = CPL - 1; c >= 0; --c) {
                 const u32 col = j + c;
-                const u32 u = sbits_order<DT>(sq_dist<D>(rx, cx[c]));
+                const u32 u = sbits_order<DT>(sd[c]);
                 const bool ok = col > i && col < n;
                 if (ok && u <= rk) {
                     rk = u;
@@ -316,14 +380,17 @@ __global__ void __launch_bounds__(CS_THREADS, 3)
                     bk[c] = bv[c] = 0xFFFFFFFFu;
                 }
                 for (u32 r = 0; r < nrows; ++r) {
-                    float rx[D];
+                    float rx[D], sd[CPC];
 #pragma unroll
                     for (int k = 0; k < D; ++k)
                         rx[k] = s_rp[r * D + k];
+#pragma unroll
+                    for (int c = 0; c < CPC; ++c)
+                        sd[c] = sq_dist<D>(rx, cx[c]);
                     const u32 vr = s_rv[r];
 #pragma unroll
                     for (int c = 0; c < CPC; ++c) {
-                        const u32 u = sbits_order<DT>(sq_dist<D>(rx, cx[c]));
+                        const u32 u = sbits_order<DT>(sd[c]);
                         if (u < bk[c] || (u == bk[c] && vr < bv[c])) {
                             bk[c] = u;
                             bv[c] = vr;
