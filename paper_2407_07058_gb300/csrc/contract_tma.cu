@@ -34,6 +34,8 @@
 #include "internal.h"
 #include "mst_device.cuh"
 
+#include <type_traits>
+
 namespace appd {
 
 namespace {
@@ -136,7 +138,7 @@ __device__ __forceinline__ u32 first_group_col(u32 row) { return ((row + 1u) >> 
 
 template <int DT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_contract_tma(ContractArgs a, u32 run_min, u32 run_max, u32* status)
+    k_contract_tma(ContractArgs a, u32 run_min, u32 run_max, u32* status, const u32* signs)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TcMeta s_meta[TC_STAGES];
@@ -289,6 +291,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 
     // ----------------------------------------------------------- consumers
+    // FP32 weights with no sign bit anywhere in the upper triangle (round 1
+    // checked every element this pass reads right of a row's diagonal)
+    // compare as raw bits, the unsigned order of their keys (CDT = DT | 1:
+    // the identity, complemented for the widest path); a column minimum is
+    // turned into its key once, at the fold.  Columns left of the item's
+    // smallest row may hold other values, but they never reach a bin.
+    const bool raw = (DT & 1) == 0 && signs != nullptr && *(volatile u32*)signs == 0u;
+    // SH: n <= SHORT_N, the pair code is lo << 16 | hi (decided once per CTA)
+    auto consumers = [&](auto cdt_tag, auto short_tag) {
+    constexpr int CDT = decltype(cdt_tag)::value;
+    constexpr bool SH = decltype(short_tag)::value;
+    // key of DT from a minimum compared under CDT
+    auto fix = [](u32 k) -> u32 {
+        if constexpr (CDT == DT)
+            return k;
+        else if constexpr (DT == 0)
+            return k | 0x80000000u;
+        else
+            return k & 0x7FFFFFFFu;
+    };
     // group t of this thread: columns c0 + 4 * ctid + 4 * TC_CONS * t .. +3
     // (interleaved, so a warp's 16-byte shared loads are contiguous)
     const u32 ctid = tid;   // 0 .. TC_CONS-1
@@ -344,14 +366,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // the item's smallest row reaches every group of the chunk
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    bk[4 * t + c] = key_of(lane_of_dyn(v[t], c), DT);
+                    bk[4 * t + c] = key_of(lane_of_dyn(v[t], c), CDT);
                     bi[4 * t + c] = row;
                 }
             } else if (j > row) {
                 // all four columns right of the row's diagonal
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const u32 kk = key_of(lane_of_dyn(v[t], c), DT);
+                    const u32 kk = key_of(lane_of_dyn(v[t], c), CDT);
                     if (kk < bk[4 * t + c]) {
                         bk[4 * t + c] = kk;
                         bi[4 * t + c] = row;
@@ -361,7 +383,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // the group that holds the row's diagonal
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const u32 kk = key_of(lane_of_dyn(v[t], c), DT);
+                    const u32 kk = key_of(lane_of_dyn(v[t], c), CDT);
                     if (j + (u32)c > row && kk < bk[4 * t + c]) {
                         bk[4 * t + c] = kk;
                         bi[4 * t + c] = row;
@@ -388,7 +410,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int c = 0; c < 4; ++c) {
                     rel[c] = L[c] - b0;
                     okc[c] = (L[c] != A) && (rel[c] < nb) && ((u32)c >= cmin);
-                    e[c] = ((u64)bk[4 * t + c] << 32) | pair_code(bi[4 * t + c], j + (u32)c, cr);
+                    const u32 code = SH ? ((bi[4 * t + c] << 16) | (j + (u32)c))
+                                       : pair_code(bi[4 * t + c], j + (u32)c, cr);
+                    e[c] = ((u64)fix(bk[4 * t + c]) << 32) | code;
                 }
                 u64 cur[4];
 #pragma unroll
@@ -434,6 +458,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     }
+    };
+    using sh_yes = std::true_type;
+    using sh_no = std::false_type;
+    const bool sh = cr <= SHORT_N;
+    if (raw) {
+        if (sh)
+            consumers(std::integral_constant<int, DT | 1>{}, sh_yes{});
+        else
+            consumers(std::integral_constant<int, DT | 1>{}, sh_no{});
+    } else {
+        if (sh)
+            consumers(std::integral_constant<int, DT>{}, sh_yes{});
+        else
+            consumers(std::integral_constant<int, DT>{}, sh_no{});
+    }
 }
 
 cudaError_t preload_contract_tma()
@@ -448,7 +487,7 @@ u32 contract_tma_bin_cap(int smem_optin)
 }
 
 cudaError_t launch_contract0_tma(const ContractArgs& ca, int dt, int blocks, u32 run_max, u32* status,
-                                 cudaStream_t s)
+                                 const u32* signs, cudaStream_t s)
 {
     const size_t smem = TC_RING_BYTES + (size_t)ca.bin_cap * sizeof(u64);
     auto k = dt == 0 ? k_contract_tma<0> : dt == 1 ? k_contract_tma<1> : dt == 2 ? k_contract_tma<2>
@@ -456,7 +495,7 @@ cudaError_t launch_contract0_tma(const ContractArgs& ca, int dt, int blocks, u32
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess)
         return err;
-    k<<<blocks, TC_THREADS, smem, s>>>(ca, 0u, run_max, status);
+    k<<<blocks, TC_THREADS, smem, s>>>(ca, 0u, run_max, status, signs);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,8 @@ struct Counters {
     u32 jump_flag[3];        // pointer-jumping convergence flags (rotating)
     u32 fill_next;           // work-queue head of the Algorithm 4 fill
     u32 fill_total;
-    u32 pad[2];
+    u32 signs;               // OR of the sign bits of W's upper triangle (FP32 round 1)
+    u32 pad;
     GridBar bar;             // grid barrier of the cooperative kernels
 };
 
@@ -128,11 +129,12 @@ cudaError_t preload_insert_tree();
 // level-0 contraction over the upper triangle fed by bulk copies
 // (contract_tma.cu); runs when |C_1| <= run_max, needs n % 4 == 0, W 16-byte
 // aligned, ca.label16 8-byte aligned (n + 8 entries, written by the level-0
-// step) and ca.bin_cap <= contract_tma_bin_cap(smem_optin)
+// step) and ca.bin_cap <= contract_tma_bin_cap(smem_optin); signs: the sign
+// word k_rowmin_sym filled for this W (FP32), or null when it did not run
 struct ContractArgs;
 u32 contract_tma_bin_cap(int smem_optin);
 cudaError_t launch_contract0_tma(const ContractArgs& ca, int dt, int blocks, u32 run_max, u32* status,
-                                 cudaStream_t s);
+                                 const u32* signs, cudaStream_t s);
 
 // profiling (appd_profile_begin/end): phases of a solve
 enum Phase { PH_ROWMIN = 0, PH_STEP, PH_CONTRACT0, PH_CONTRACT, PH_LEAF, PH_FILL, PH_BATCHED, PH_COUNT };

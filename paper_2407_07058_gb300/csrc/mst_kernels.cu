@@ -61,9 +61,16 @@ __global__ void __launch_bounds__(256) k_rowmin(const u32* __restrict__ W, u32 n
 // every unordered pair is read once (half of W).  best[] starts at +inf.
 constexpr u32 RS_ROWS = 256, RS_COLS = 1024;
 
+// FP32 inputs: the pass also records in *signs whether any element it uses
+// has its sign bit set, so that the level-0 contraction knows whether every
+// weight of the upper triangle is a non-negative float (or a NaN with the
+// sign bit clear), whose raw bits already compare in the order of their
+// keys.  Minimax keys of such floats have the top bit set, so the smallest
+// row minimum tells (one minimum per row); the widest keys are complemented
+// and ORing the raw bits tells instead.
 template <int DT>
 __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u32 n,
-                                                    u64* __restrict__ best)
+                                                    u64* __restrict__ best, u32* __restrict__ signs)
 {
     __shared__ u64 s_row[RS_ROWS];
     const u32 i0 = blockIdx.y * RS_ROWS, c0 = blockIdx.x * RS_COLS;
@@ -84,6 +91,8 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
     // column); starting from key 0xFFFFFFFF the first valid row always enters.
     u32 ck[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
     u32 ci[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    u32 sg = 0;             // widest FP32: OR of the raw bits
+    u32 smin = 0xFFFFFFFFu;  // minimax FP32: smallest row minimum key
     for (int pass = RS_ROWS / 32 - 1; pass >= 0; --pass) {
         const u32 ib = i0 + 32 * pass;
         if (ib >= imax)
@@ -107,6 +116,8 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
                     const u32 k[4] = {key_of(v[q].x, DT), key_of(v[q].y, DT), key_of(v[q].z, DT),
                                       key_of(v[q].w, DT)};
                     if (!mask) {
+                        if constexpr (DT == 2)
+                            sg |= v[q].x | v[q].y | v[q].z | v[q].w;
 #pragma unroll
                         for (int c = 3; c >= 0; --c)
                             if (k[c] <= rk) {
@@ -120,6 +131,12 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
                                 ci[c] = i;
                             }
                     } else {
+                        if constexpr (DT == 2) {
+                            const u32 e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                sg |= j + c > i ? e[c] : 0u;
+                        }
 #pragma unroll
                         for (int c = 3; c >= 0; --c)
                             if (j + c > i && k[c] <= rk) {
@@ -140,9 +157,17 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
                 const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, rk == kmin ? rj : 0xFFFFFFFFu);
                 if (lane == r && jmin != 0xFFFFFFFFu)
                     atomicMin(&s_row[32 * pass + r], ((u64)kmin << 32) | jmin);
+                if constexpr (DT == 0)
+                    smin = min(smin, kmin);
             }
         }
     }
+    if constexpr (DT == 0)
+        if (lane == 0 && smin < 0x80000000u)
+            atomicOr(signs, 1u);
+    if constexpr (DT == 2)
+        if (__any_sync(0xFFFFFFFFu, sg >> 31) && lane == 0)
+            atomicOr(signs, 1u);
     // column candidates: edge (i, j) with i the smallest-key row (ties: lower i)
     if (live) {
 #pragma unroll
@@ -412,6 +437,7 @@ __global__ void k_mst_init(Counters* ctr, u32* comp, u32 n, u32 bar_reset)
         ctr->total_chunks = 0;
         ctr->nbr = 0;
         ctr->jump_flag[0] = ctr->jump_flag[1] = ctr->jump_flag[2] = 0;
+        ctr->signs = 0;
         if (bar_reset) {
             ctr->bar.count = 0;
             ctr->bar.abort = 0;
@@ -513,7 +539,7 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
         dim3 grid((n + RS_COLS - 1) / RS_COLS, (n + RS_ROWS - 1) / RS_ROWS);
         auto kr = dt == 0 ? k_rowmin_sym<0> : dt == 1 ? k_rowmin_sym<1> : dt == 2 ? k_rowmin_sym<2>
                                                                                 : k_rowmin_sym<3>;
-        kr<<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0]);
+        kr<<<grid, 256, 0, s>>>((const u32*)W, n, ws.best[0], &ws.ctr->signs);
         if ((err = cudaGetLastError()) != cudaSuccess)
             return err;
     } else {
@@ -638,8 +664,8 @@ cudaError_t run_mst(Workspace& ws, const void* W, int dt, void* cbuf, size_t cbu
             ContractArgs cat = ca;
             cat.bin_cap = ws.bin_cap_t;
             cat.label16 = ws.label16;
-            if ((err = launch_contract0_tma(cat, dt, ws.contract_blocks, ws.bin_cap_t, status, s)) !=
-                cudaSuccess)
+            err = launch_contract0_tma(cat, dt, ws.contract_blocks, ws.bin_cap_t, status, &ws.ctr->signs, s);
+            if (err != cudaSuccess)
                 return err;
             k0b<<<ws.contract_blocks, CONTRACT_THREADS, smem, s>>>(ca1, ws.bin_cap_t + 1, 0xFFFFFFFFu);
             prof_launches(1);

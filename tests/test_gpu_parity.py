@@ -232,3 +232,29 @@ def test_batched_repeat_replays_and_tuning():
                 got = Mh[offs[g]: offs[g] + n * n].reshape(n, n).view(np.float32)
                 assert_bits(got, refs[g], f"graph {g} tuning {tuning}")
     appd.batched_tuning()
+
+
+@pytest.mark.parametrize("n", [64, 1000, 4096, 8192])
+@pytest.mark.parametrize("case", ["nonneg", "one_neg_zero", "one_negative", "neg_diagonal", "pos_nan"])
+@pytest.mark.parametrize("widest", [False, True])
+def test_sign_check_of_round_one(n, case, widest):
+    """FP32 weights whose upper triangle has no sign bit are compared as raw
+    bits in the level-0 contraction; one sign bit anywhere in the upper
+    triangle (-0.0 included) must switch it back to the key order.  A
+    negative diagonal is never read; a NaN with the sign bit clear keeps the
+    raw order (it is the largest key)."""
+    rng = np.random.default_rng(31 * n + len(case))
+    W = sym_random(n, rng, np.float32)
+    i, j = sorted(rng.choice(n, 2, replace=False))
+    if case == "one_neg_zero":
+        W[i, j] = W[j, i] = np.float32(-0.0)
+    elif case == "one_negative":
+        W[i, j] = W[j, i] = np.float32(-0.25)
+    elif case == "neg_diagonal":
+        np.fill_diagonal(W, np.float32(-1.0))
+    elif case == "pos_nan":
+        W[i, j] = W[j, i] = np.uint32(0x7FC00000).view(np.float32)
+    M = appd.solve(to_dev(W), widest=widest)
+    torch.cuda.synchronize()
+    assert appd.last_device_status() == 0
+    assert_bits(from_dev(M, W), oracle.appd(W, widest=widest), f"n={n} {case} widest={widest}")

@@ -8,7 +8,10 @@ the oracle's own pair numbering) and the whole MST edge set, at
 - n = 92682, the largest n the 32-bit pair rank allows: FP32 distances of
   16-D mixture points (W and M together 68.7 GB on the device);
 - n = 70001 uint32 weights with heavy ties: n odd, so rows are not 16-byte
-  aligned and the unaligned forms of round 1 and the level-0 contraction run.
+  aligned and the unaligned forms of round 1 and the level-0 contraction run;
+- n = 65540 FP32 mixture distances: rows 16-byte aligned and C_1 small enough
+  for the bulk-copy contraction, so its fold forms pair ranks (and compares
+  raw bits: no weight is negative).
 """
 import numpy as np
 import pytest
@@ -55,6 +58,18 @@ def test_largest_n_gmm16_every_row():
     assert appd.last_device_status() == 0
     assert int(torch.count_nonzero(torch.diagonal(M))) == 0
     _check(W, M, W.cpu().numpy(), f"n={n} gmm16")
+
+
+def test_aligned_n_above_16_bits_bulk_copy_contraction_every_row():
+    n = 65540
+    st = torch.cuda.current_stream().cuda_stream
+    pts = torch.from_numpy(synth.gmm_points(n, 16, 32, sigma=1.0, seed=6, mean_std=5.0)).cuda()
+    W = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    synth.device_euclid(pts.data_ptr(), n, 16, W.data_ptr(), st)
+    M = appd.solve(W)
+    torch.cuda.synchronize()
+    assert appd.last_device_status() == 0
+    _check(W, M, W.cpu().numpy(), f"n={n} gmm16 aligned")
 
 
 def test_odd_n_above_16_bits_uint32_ties_every_row():
