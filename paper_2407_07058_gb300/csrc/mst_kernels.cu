@@ -65,11 +65,16 @@ constexpr u32 RS_ROWS = 256, RS_COLS = 1024;
 // has its sign bit set, so that the level-0 contraction knows whether every
 // weight of the upper triangle is a non-negative float (or a NaN with the
 // sign bit clear), whose raw bits already compare in the order of their
-// keys.  Minimax keys of such floats have the top bit set, so the smallest
-// row minimum tells (one minimum per row); the widest keys are complemented
-// and ORing the raw bits tells instead.
+// keys.  Minimax: a warp off the diagonal compares raw bits itself while
+// every batch of eight rows it loads has no sign bit (one OR per element
+// instead of the two-instruction key); the first batch with one switches
+// the warp to keys for the rest of its slab (its column minima, raw bits
+// of non-negative floats, become keys by setting the top bit).  Warps on
+// the diagonal use keys throughout and report a sign bit through their
+// smallest row minimum (a key below 2^31).  Widest keys are complemented;
+// an OR of the raw bits reports it there.
 template <int DT>
-__global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u32 n,
+__global__ void __launch_bounds__(256, 4) k_rowmin_sym(const u32* __restrict__ W, u32 n,
                                                     u64* __restrict__ best, u32* __restrict__ signs)
 {
     __shared__ u64 s_row[RS_ROWS];
@@ -91,8 +96,69 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
     // column); starting from key 0xFFFFFFFF the first valid row always enters.
     u32 ck[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
     u32 ci[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-    u32 sg = 0;             // widest FP32: OR of the raw bits
-    u32 smin = 0xFFFFFFFFu;  // minimax FP32: smallest row minimum key
+    u32 sg = 0;              // widest FP32: OR of the raw bits
+    u32 smin = 0xFFFFFFFFu;  // minimax FP32, keyed warps: smallest row minimum key
+    bool keyed = DT != 0 || mask;   // warp-uniform
+    // one batch of eight loaded rows (descending), compared under CDT; raw
+    // minimax minima (CDT != DT) become keys by setting the top bit
+    auto consume = [&](const uint4 (&v)[8], u32 ib, int pass, int r8, auto cdt_tag) {
+        constexpr int CDT = decltype(cdt_tag)::value;
+#pragma unroll
+        for (int q = 7; q >= 0; --q) {
+            const u32 r = r8 + q, i = ib + r;
+            // row i's minimum over this lane's columns, same rule over
+            // descending columns: the smallest key at the smallest column
+            u32 rk = 0xFFFFFFFFu, rj = 0xFFFFFFFFu;
+            if (live && i < imax) {
+                const u32 k[4] = {key_of(v[q].x, CDT), key_of(v[q].y, CDT), key_of(v[q].z, CDT),
+                                  key_of(v[q].w, CDT)};
+                if (!mask) {
+                    if constexpr (DT == 2)
+                        sg |= v[q].x | v[q].y | v[q].z | v[q].w;
+#pragma unroll
+                    for (int c = 3; c >= 0; --c)
+                        if (k[c] <= rk) {
+                            rk = k[c];
+                            rj = j + c;
+                        }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (k[c] <= ck[c]) {
+                            ck[c] = k[c];
+                            ci[c] = i;
+                        }
+                } else {
+                    if constexpr (DT == 2) {
+                        const u32 e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            sg |= j + c > i ? e[c] : 0u;
+                    }
+#pragma unroll
+                    for (int c = 3; c >= 0; --c)
+                        if (j + c > i && k[c] <= rk) {
+                            rk = k[c];
+                            rj = j + c;
+                        }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (j + c > i && k[c] <= ck[c]) {
+                            ck[c] = k[c];
+                            ci[c] = i;
+                        }
+                }
+            }
+            // warp minimum of (key, column) for row i: smallest key, then the
+            // smallest column among the lanes holding it
+            const u32 kmin = __reduce_min_sync(0xFFFFFFFFu, rk);
+            const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, rk == kmin ? rj : 0xFFFFFFFFu);
+            const u32 kkey = CDT == DT ? kmin : (kmin | 0x80000000u);
+            if (lane == r && jmin != 0xFFFFFFFFu)
+                atomicMin(&s_row[32 * pass + r], ((u64)kkey << 32) | jmin);
+            if constexpr (DT == 0 && CDT == DT)
+                smin = min(smin, kmin);
+        }
+    };
     for (int pass = RS_ROWS / 32 - 1; pass >= 0; --pass) {
         const u32 ib = i0 + 32 * pass;
         if (ib >= imax)
@@ -106,65 +172,38 @@ __global__ void __launch_bounds__(256) k_rowmin_sym(const u32* __restrict__ W, u
                 if (live && i < imax)
                     v[q] = ld_stream_v4(W + (size_t)i * n + j);
             }
+            if constexpr (DT == 0) {
+                if (!keyed) {
+                    u32 o = 0;
 #pragma unroll
-            for (int q = 7; q >= 0; --q) {
-                const u32 r = r8 + q, i = ib + r;
-                // row i's minimum over this lane's columns, same rule over
-                // descending columns: the smallest key at the smallest column
-                u32 rk = 0xFFFFFFFFu, rj = 0xFFFFFFFFu;
-                if (live && i < imax) {
-                    const u32 k[4] = {key_of(v[q].x, DT), key_of(v[q].y, DT), key_of(v[q].z, DT),
-                                      key_of(v[q].w, DT)};
-                    if (!mask) {
-                        if constexpr (DT == 2)
-                            sg |= v[q].x | v[q].y | v[q].z | v[q].w;
-#pragma unroll
-                        for (int c = 3; c >= 0; --c)
-                            if (k[c] <= rk) {
-                                rk = k[c];
-                                rj = j + c;
-                            }
+                    for (u32 q = 0; q < 8; ++q)
+                        if (live && ib + r8 + q < imax)
+                            o |= v[q].x | v[q].y | v[q].z | v[q].w;
+                    if (__any_sync(0xFFFFFFFFu, o >> 31)) {
+                        keyed = true;
 #pragma unroll
                         for (int c = 0; c < 4; ++c)
-                            if (k[c] <= ck[c]) {
-                                ck[c] = k[c];
-                                ci[c] = i;
-                            }
-                    } else {
-                        if constexpr (DT == 2) {
-                            const u32 e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-#pragma unroll
-                            for (int c = 0; c < 4; ++c)
-                                sg |= j + c > i ? e[c] : 0u;
-                        }
-#pragma unroll
-                        for (int c = 3; c >= 0; --c)
-                            if (j + c > i && k[c] <= rk) {
-                                rk = k[c];
-                                rj = j + c;
-                            }
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (j + c > i && k[c] <= ck[c]) {
-                                ck[c] = k[c];
-                                ci[c] = i;
-                            }
+                            ck[c] |= 0x80000000u;
+                        if (lane == 0)
+                            atomicOr(signs, 1u);
                     }
                 }
-                // warp minimum of (key, column) for row i: smallest key, then the
-                // smallest column among the lanes holding it
-                const u32 kmin = __reduce_min_sync(0xFFFFFFFFu, rk);
-                const u32 jmin = __reduce_min_sync(0xFFFFFFFFu, rk == kmin ? rj : 0xFFFFFFFFu);
-                if (lane == r && jmin != 0xFFFFFFFFu)
-                    atomicMin(&s_row[32 * pass + r], ((u64)kmin << 32) | jmin);
-                if constexpr (DT == 0)
-                    smin = min(smin, kmin);
+                if (!keyed) {
+                    consume(v, ib, pass, r8, std::integral_constant<int, 1>{});
+                    continue;
+                }
             }
+            consume(v, ib, pass, r8, std::integral_constant<int, DT>{});
         }
     }
-    if constexpr (DT == 0)
+    if constexpr (DT == 0) {
+        if (!keyed)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                ck[c] |= 0x80000000u;
         if (lane == 0 && smin < 0x80000000u)
             atomicOr(signs, 1u);
+    }
     if constexpr (DT == 2)
         if (__any_sync(0xFFFFFFFFu, sg >> 31) && lane == 0)
             atomicOr(signs, 1u);
