@@ -41,14 +41,16 @@ WIDEST = 2   # flag: reverse the order (widest paths)
 
 
 def build() -> str:
-    """Compile the oracle with gcc (plain C, -O2, no FMA contraction)."""
+    """Compile the oracle with gcc (plain C, -O2, no FMA contraction; OpenMP
+    only spreads the independent rows of prim_rows and points_w over the
+    cores)."""
     os.makedirs(_BUILD, exist_ok=True)
     out = os.path.join(_BUILD, "liboracle.so")
     src = os.path.join(_HERE, "appd_oracle.c")
     if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-shared", "-fPIC",
-                               "-o", tmp, src, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fopenmp", "-shared",
+                               "-fPIC", "-o", tmp, src, "-lm"])
         os.replace(tmp, out)
     return out
 

@@ -688,6 +688,25 @@ int appd_oracle_tree_rows(const uint32_t *W, int64_t n, int dtype, const uint64_
  * Mutation 5 leaves out the edge that added the farther vertex (an
  * off-by-one in the range), which a pin must catch.
  */
+/* edge_bits of a running maximum, looked up again only when it changes
+ * (a row's running maximum takes few distinct values; each lookup decodes
+ * the pair number and reads W) */
+typedef struct {
+    int have;
+    uint64_t code;
+    uint32_t bits;
+} bits_memo;
+
+static uint32_t edge_bits_memo(const uint32_t *W, int64_t n, uint64_t code, bits_memo *m)
+{
+    if (!m->have || m->code != code) {
+        m->have = 1;
+        m->code = code;
+        m->bits = edge_bits(W, n, code);
+    }
+    return m->bits;
+}
+
 int appd_oracle_prim_rows(const uint32_t *W, int64_t n, int dtype, const uint64_t *mst,
                           const uint32_t *order, const uint32_t *src, int64_t nsrc, uint32_t *rows)
 {
@@ -699,10 +718,13 @@ int appd_oracle_prim_rows(const uint32_t *W, int64_t n, int dtype, const uint64_
         return -2;
     for (int64_t k = 0; k < n; ++k)
         rank[order[k]] = k;
+    /* rows are independent: one per thread (a plain parallel map) */
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nsrc; ++t) {
         const int64_t a = rank[src[t]];
         uint32_t *row = rows + t * n;
         row[src[t]] = 0;
+        bits_memo memo = {0, 0, 0};
         /* later vertices: running maximum of delta_{a+1..b} */
         uint64_t best = 0;
         for (int64_t b = a + 1; b < n; ++b) {
@@ -710,12 +732,12 @@ int appd_oracle_prim_rows(const uint32_t *W, int64_t n, int dtype, const uint64_
             if (g_mutation == 5) {
                 if (b > a + 1 && mst[b - 2] > best)
                     best = mst[b - 2];
-                row[order[b]] = edge_bits(W, n, b > a + 1 ? best : d);
+                row[order[b]] = edge_bits_memo(W, n, b > a + 1 ? best : d, &memo);
                 continue;
             }
             if (b == a + 1 || d > best)
                 best = d;
-            row[order[b]] = edge_bits(W, n, best);
+            row[order[b]] = edge_bits_memo(W, n, best, &memo);
         }
         /* earlier vertices: running maximum of delta_{b+1..a} */
         best = 0;
@@ -723,7 +745,7 @@ int appd_oracle_prim_rows(const uint32_t *W, int64_t n, int dtype, const uint64_
             const uint64_t d = mst[b];
             if (b == a - 1 || d > best)
                 best = d;
-            row[order[b]] = edge_bits(W, n, best);
+            row[order[b]] = edge_bits_memo(W, n, best, &memo);
         }
     }
     free(rank);
@@ -745,6 +767,8 @@ int appd_oracle_points_w(const float *X, int64_t n, int d, uint32_t *W)
 {
     if (n < 0 || d < 1)
         return -1;
+    /* rows are independent: one per thread (a plain parallel map) */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t j = 0; j < n; ++j) {
             float s = 0.0f;
