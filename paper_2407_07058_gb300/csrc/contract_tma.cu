@@ -337,7 +337,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const u32 flags = w0.w;
         if (flags & TF_END)
             break;
-        const uint4 w1 = mr[1], w2 = mr[2];
+        // the item's fields are read only at a chunk's last row (the fold and
+        // the item's end)
+        uint4 w1 = make_uint4(0u, 0u, 0u, 0u), w2 = w1;
+        if (flags & TF_LAST) {
+            w1 = mr[1];
+            w2 = mr[2];
+        }
         const u32 c0 = w0.x, c1 = w0.y, row = w0.z;
         const u32 A = w1.x, b0 = w1.y, nb = w1.z, single = w1.w, r0 = w2.x;
         const unsigned char* st = ring + slot * TC_STAGE_BYTES;
@@ -357,6 +363,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (u32 t = 0; t < TC_G; ++t)
             v[t] = rows[ctid + TC_CONS * t];
         const bool first = (flags & TF_FIRST) != 0;
+        const u32 jf = c0 + 4u * ctid, jl = jf + 4u * TC_CONS * (TC_G - 1);
+        if (!first && jf > row && jl < c1) {
+            // every group of this thread lies right of the row's diagonal
+#pragma unroll
+            for (u32 t = 0; t < TC_G; ++t)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const u32 kk = key_of(lane_of_dyn(v[t], c), CDT);
+                    if (kk < bk[4 * t + c]) {
+                        bk[4 * t + c] = kk;
+                        bi[4 * t + c] = row;
+                    }
+                }
+        } else
 #pragma unroll
         for (u32 t = 0; t < TC_G; ++t) {
             const u32 j = c0 + 4u * (ctid + TC_CONS * t);
