@@ -7,7 +7,7 @@
 namespace appd {
 
 constexpr int FC = 128;   // columns per CTA
-constexpr int FT = 256;   // threads per CTA
+constexpr int FT = 512;   // threads per CTA (32 warps per SM at two CTAs: more stores in flight)
 
 __device__ __forceinline__ u32 rmq_gap(const u32* __restrict__ st, u32 stride, u32 a, u32 b)
 {
