@@ -40,3 +40,24 @@ def test_reference_arm_other_ranks_exit_quietly():
              {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_stored_traffic_is_reported_only_while_its_sources_are_unchanged(tmp_path, monkeypatch):
+    """bench.ncu_traffic gives the recorded DRAM bytes of a kernel while the
+    hash of the sources listed beside them matches, and None once one of
+    them changed (the counters would no longer describe the kernel)."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source v1\n")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(
+        {"k_demo": {"sources": ["k.cu"], "source_sha256_16": h, "bytes_per_launch_full": 123.0}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic("k_demo") == 123.0
+    assert bench.ncu_traffic("k_other") is None
+    src.write_text("kernel source v2\n")
+    assert bench.ncu_traffic("k_demo") is None
+
